@@ -1,0 +1,362 @@
+"""Benchmark of the BO suggest step on GB300: candidates scored per second.
+
+One step = one observation update of the surrogate (FP64 L^-1 / beta) plus
+one prediction pass over every valid configuration (K* tiles, contraction,
+row reduction, lambda, EI / PI / LCB, masked top-k): every row of the hot
+path.  Workload (default): the 7-parameter GEMM-tiling-like space, 113,247
+valid of 245,760 configurations, at n = 220 - K .. 220 observations.
+
+  python bench.py [--steps K] [--warmup W] [--precision fp64|fp16x3|bf16x3|tf32]
+                  [--config 1|2|3] [--impl ours|reference] [--gpus N]
+
+Prints one JSON line (rank 0).  `value` is device time (CUDA events on the
+session's stream) with the space's state resident in HBM and L2 flushed
+between steps; `e2e` goes through the C ABI (bo_observe + bo_suggest: the
+observation in, the pass result out) timed on the host.  Under torchrun each
+rank runs an independent replica (the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidates scored/s per suggest & p50/p99 suggest latency vs plain FP64 form"
+CONFIGS = {
+    1: dict(name="blocks-4p: 4 params, 2,560 valid of 5,120", n_final=80, af="ei"),
+    2: dict(name="gemm-7p: 7 params, 113,247 valid of 245,760", n_final=220, af="ei"),
+    3: dict(name="gemm-9p: 9 params, 1,032,469 valid of 3,932,160", n_final=512, af="ei"),
+}
+DTYPE = {"fp64": "f64", "fp16x3": "f16x3 (fp32 accumulate)", "bf16x3": "bf16x3 (fp32 accumulate)",
+         "tf32": "tf32 (fp32 accumulate)"}
+# FP64 peak: the recipe's nominal GB300 figure (no measured FP64 peak exists for this machine)
+FP64_PEAK_TFLOPS = 1.25
+# dram bytes per launch of the dominant kernel from an ncu capture, keyed by the
+# sha256 of the kernel source it was taken on (null once the source changes)
+TRAFFIC = {}
+
+
+def space_for(cfg):
+    from paper_2111_14991_gb300 import workloads as W
+    return {1: W.config1_space, 2: W.config2_space, 3: W.config3_space}[cfg]()
+
+
+def observations(sp, cfg, count, seed=0):
+    from paper_2111_14991_gb300 import workloads as W
+    land = W.Landscape(sp, seed)
+    idx = W.clustered_observations(land, count, seed)
+    y = np.array([land(i) for i in idx])
+    return idx, y
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                sm.append(float(f[1]))
+                mx = float(f[2])
+                for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                      "sw_power_cap"), f[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        except (OSError, ValueError):
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_sha(precision):
+    src = "bo_predict_f64.cu" if precision == "fp64" else "bo_predict_tc.cu"
+    path = os.path.join(ROOT, "paper_2111_14991_gb300", "csrc", src)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def flops_per_candidate(n, d):
+    """Algorithmic flops of one candidate: the triangular contraction n(n+1),
+    the row reductions 4n, and the Matern cross-covariance n(3d + 12)."""
+    return n * (n + 1) + 4 * n + n * (3 * d + 12)
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2111_14991_gb300 import Space, build
+    build.build()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    cfg = CONFIGS[args.config]
+    sp = space_for(args.config)
+    steps, warm = args.steps, args.warmup
+    n_final = cfg["n_final"]
+    idx, y = observations(sp, args.config, n_final, seed=0)
+    n0 = max(2, n_final - steps - warm)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def fresh():
+        s = Space(sp.grids, sp.invalid, af=cfg["af"], precision=args.precision, n_max=max(n_final, 32))
+        for i, v in zip(idx[:n0], y[:n0]):
+            s.observe(int(i), float(v))
+        s.sync()
+        return s
+
+    # ---- device-resident steps: observe + predict + acquire, events on the stream
+    s = fresh()
+    times, scored, launches = [], 0, 0
+    with ClockSampler(dev) as clk:
+        for t in range(warm + steps):
+            j = n0 + t
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = s.launch_count()
+            e0.record(stream)
+            s.replay_enqueue([idx[j]], [y[j]])
+            e1.record(stream)
+            r = s.replay_fetch(1)[0]
+            if t >= warm:
+                times.append(e0.elapsed_time(e1) / 1e3)
+                scored += r["n_scored"]
+                launches += s.launch_count() - l0
+    clocks = clk.summary()
+    # ---- the dominant kernel alone (prediction pass) for the roofline
+    k1 = []
+    for _ in range(max(3, min(10, steps))):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.predict_enqueue()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        k1.append(e0.elapsed_time(e1) / 1e3)
+    n_last = n0 + warm + steps
+    N = sp.n_valid
+    k1_time = statistics.median(k1)
+    s.close()
+
+    # ---- end to end through the C ABI: observe (in) + suggest (result out), host clock
+    s = fresh()
+    for t in range(warm):
+        j = n0 + t
+        s.observe(int(idx[j]), float(y[j]))
+        s.suggest()
+    e2e_t, e2e_scored = [], 0
+    for t in range(steps):
+        j = n0 + warm + t
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.observe(int(idx[j]), float(y[j]))
+        info = s.suggest()
+        t1 = time.perf_counter()
+        e2e_t.append(t1 - t0)
+        e2e_scored += info["n_scored"]
+    # suggest latency at the final state (single AF: every call is a full pass)
+    lat = []
+    s2 = Space(sp.grids, sp.invalid, af="ei", precision=args.precision, n_max=max(n_final, 32))
+    for i, v in zip(idx[:n_last], y[:n_last]):
+        s2.observe(int(i), float(v))
+    reps = max(args.latency_reps, steps)
+    for t in range(10 + reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2.suggest()
+        if t >= 10:
+            lat.append(time.perf_counter() - t0)
+    s.close()
+    s2.close()
+
+    # ---- aggregate over ranks: max time
+    tot = sum(times)
+    e2e_tot = sum(e2e_t)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([tot, e2e_tot], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot, e2e_tot = tt.tolist()
+    value = scored * world / tot
+    e2e_value = e2e_scored * world / e2e_tot
+    n_mid = n_last - steps // 2
+    fl = flops_per_candidate(n_last, sp.d) * N
+    achieved = fl / k1_time / 1e12
+    roofline = None
+    if args.precision == "fp64":
+        sha = kernel_sha(args.precision)
+        tr = TRAFFIC.get("predict_f64")
+        roofline = {"bound": "alu", "kernel": "predict_f64_kernel", "achieved": round(achieved, 4),
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                    "peak_source": "nominal GB300 FP64 (recipe table); no measured FP64 peak",
+                    "traffic": tr["bytes_per_launch"] if tr and tr["src_sha"] == sha else None,
+                    "flops_per_launch": fl, "launch_s": k1_time}
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "candidates/s", "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": round(1e3 * tot / steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[args.precision], "data": "synthetic (seeded landscape, clustered BO-like trace)",
+        "config": {"workload": cfg["name"], "n_obs": f"{n0 + warm + 1}..{n_last}", "n_mid": n_mid,
+                   "precision": args.precision, "af_pass": "ei+poi+lcb top-3 each",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": round(1e3 * float(np.percentile(lat, 50)), 4),
+                       "p99": round(1e3 * float(np.percentile(lat, 99)), 4), "calls": len(lat),
+                       "what": "bo_suggest host entry to index returned, n = %d" % n_last},
+        "e2e": {"value": round(e2e_value, 1), "unit": "candidates/s", "h2d_bytes_per_step": 16,
+                "d2h_bytes_per_step": 400, "what": "bo_observe(idx, y) + bo_suggest, host clock"},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+    return out
+
+
+def cpu_baseline(cfg_id, budget_s=15.0):
+    """The oracle, as it stands, on the host: one suggest's prediction + scores
+    over a bounded sample of the candidates at the final state."""
+    import oracle as O
+    sp = space_for(cfg_id)
+    cfg = CONFIGS[cfg_id]
+    idx, y = observations(sp, cfg_id, cfg["n_final"], seed=0)
+    coords = sp.valid_coords()
+    t0 = time.perf_counter()
+    fit = O.gp_fit(coords[idx], y, 1.5, 1.5, 1e-10)
+    t_fit = time.perf_counter() - t0
+    rng = np.random.default_rng(1)
+    sample = min(sp.n_valid, 20000)
+    done, t_pred = 0, 0.0
+    while t_pred < budget_s and done < sp.n_valid:
+        sel = rng.choice(sp.n_valid, sample, replace=False)
+        t0 = time.perf_counter()
+        mu, var = O.gp_posterior(fit, coords[sel])
+        sd = np.sqrt(var)
+        for af in ("ei", "poi", "lcb"):
+            sc = O.acquisition(af, mu, sd, float(np.min((y - y.mean()) / y.std())), 0.1)
+            O.masked_topk(sc, np.ones(len(sel), bool), 3)
+        t_pred += time.perf_counter() - t0
+        done += sample
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max(int(i.get("num_threads", 1)) for i in threadpool_info()) or cores
+    except Exception:
+        pass
+    return {"value": round(done / (t_pred + t_fit * done / sp.n_valid), 1), "unit": "candidates/s",
+            "cores": cores, "kind": "oracle",
+            "sample": f"{done} random candidates of {sp.n_valid} at n = {cfg['n_final']} "
+                      f"(fit once, {t_pred:.1f} s of prediction + EI/PI/LCB top-3)"}
+
+
+def run_reference(args):
+    import oracle as O
+    cfg = CONFIGS[args.config]
+    sp = space_for(args.config)
+    idx, y = observations(sp, args.config, cfg["n_final"], seed=0)
+    coords = sp.valid_coords()
+    per_step = max(2000, min(sp.n_valid, 20000))
+    rng = np.random.default_rng(2)
+    times = []
+    for t in range(args.warmup + args.steps):
+        n = cfg["n_final"] - (args.steps - t) if t >= args.warmup else cfg["n_final"] - args.steps
+        n = max(2, n)
+        sel = rng.choice(sp.n_valid, per_step, replace=False)
+        t0 = time.perf_counter()
+        fit = O.gp_fit(coords[idx[:n]], y[:n], 1.5, 1.5, 1e-10)
+        mu, var = O.gp_posterior(fit, coords[sel])
+        sd = np.sqrt(var)
+        for af in ("ei", "poi", "lcb"):
+            O.masked_topk(O.acquisition(af, mu, sd, -1.0, 0.1), np.ones(per_step, bool), 3)
+        if t >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = per_step * len(times) / sum(times)
+    cores = os.cpu_count()
+    out = {"metric": METRIC, "value": round(value, 1), "unit": "candidates/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": cfg["name"], "precision": "fp64 (CPU oracle)"},
+           "cpu_baseline": {"value": round(value, 1), "unit": "candidates/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{per_step} random candidates per step, fit + predict + 3 AFs"},
+           "e2e": {"value": round(value, 1), "unit": "candidates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", type=int, default=2, choices=sorted(CONFIGS))
+    ap.add_argument("--precision", default="fp64", choices=sorted(DTYPE))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--latency-reps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+        dist.barrier()
+    out = run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.config)
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

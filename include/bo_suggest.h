@@ -1,0 +1,200 @@
+/*
+ * bo_suggest.h -- C ABI of the GB300 Bayesian-optimization suggest library.
+ *
+ * The library implements the per-iteration step of the GPU-kernel tuner of
+ * Willemsen, van Nieuwpoort and van Werkhoven, "Bayesian Optimization for
+ * auto-tuning GPU kernels":
+ *   - a discrete, normalized, constrained search space (Sec. III-D);
+ *   - a zero-mean Gaussian-process surrogate with a fixed-lengthscale Matern
+ *     covariance (Sec. III-B), updated one observation at a time;
+ *   - exhaustive prediction of every valid, non-evaluated configuration and
+ *     the acquisition functions EI, PI and LCB (Sec. III-C, III-G) with the
+ *     contextual-variance exploration factor (Sec. III-F);
+ *   - the masked argmax, and the 'multi' / 'advanced multi' selection of
+ *     acquisition functions (Sec. III-G).
+ *
+ * Conventions for every entry point:
+ *   - Return value: BO_OK (0) or one of the BO_ERR_* codes below; on error a
+ *     message is available from bo_last_error() on the calling thread, and
+ *     no output argument has been written unless stated otherwise.
+ *   - Indices are positions in the *valid list*: the valid configurations of
+ *     the Cartesian product of the parameter lists, enumerated row-major with
+ *     the last parameter fastest, restricted configurations removed.
+ *   - Host pointers are plain host memory owned by the caller unless the
+ *     argument says "device".  Arrays passed to bo_space_create are copied.
+ *   - All device work of a space is ordered on the stream given at creation.
+ *     A space may be used by one host thread at a time.
+ */
+#ifndef BO_SUGGEST_H
+#define BO_SUGGEST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+  BO_OK = 0,
+  BO_ERR_ARG = 1,          /* invalid argument or descriptor field            */
+  BO_ERR_INDEX = 2,        /* valid-list index out of range                   */
+  BO_ERR_DUPLICATE = 3,    /* configuration already observed (Sec. III-D)     */
+  BO_ERR_EXHAUSTED = 4,    /* no valid, non-evaluated configuration left      */
+  BO_ERR_NUMERIC = 5,      /* non-positive Cholesky pivot / non-finite value  */
+  BO_ERR_NOMEM = 6,        /* device or host allocation failed                */
+  BO_ERR_CUDA = 7,         /* a CUDA call failed                              */
+  BO_ERR_TIMEOUT = 8,      /* a bounded device wait ran out                   */
+  BO_ERR_NOT_POSITIVE = 9, /* contextual variance needs f+ > 0 and mu_s > 0   */
+  BO_ERR_STATE = 10,       /* call not allowed in the current state           */
+  BO_ERR_CAPACITY = 11     /* more valid observations than n_max              */
+};
+
+/* acquisition function / selection mode (Sec. III-C, III-G) */
+enum { BO_AF_EI = 0, BO_AF_PI = 1, BO_AF_LCB = 2, BO_AF_MULTI = 3, BO_AF_ADV_MULTI = 4 };
+/* exploration factor: contextual variance (Sec. III-F) or a constant */
+enum { BO_EXPLORE_CV = 0, BO_EXPLORE_CONST = 1 };
+/* observation normalization before fitting */
+enum { BO_YNORM_STANDARDIZE = 0, BO_YNORM_NONE = 1 };
+/* arithmetic of the K* . L^-T contraction (Cholesky, L^-1, beta are FP64 always) */
+enum {
+  BO_PREC_FP64 = 0,    /* FP64 on CUDA cores                                       */
+  BO_PREC_FP16X3 = 1,  /* tcgen05 f16 hi/lo split, 3 products, FP32 accumulate     */
+  BO_PREC_BF16X3 = 2,  /* tcgen05 bf16 hi/lo split, 3 products, FP32 accumulate    */
+  BO_PREC_TF32 = 3     /* tcgen05 tf32, 1 product, FP32 accumulate                 */
+};
+
+#define BO_MAX_PARAMS 16   /* parameters per space                             */
+#define BO_MAX_VALUES 256  /* values per parameter (codes are uint8)          */
+#define BO_MAX_OBS 512     /* largest n_max (valid observations fitted)        */
+
+/* Device memory provider.  alloc returns device memory of at least `bytes`
+ * bytes usable on `stream` (NULL on failure); free releases it.  With
+ * alloc == NULL the library uses cudaMallocAsync/cudaFreeAsync on the
+ * space's stream. */
+typedef void* (*bo_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*bo_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+typedef struct bo_space_desc {
+  int32_t d;                      /* number of parameters, 1..BO_MAX_PARAMS          */
+  const int32_t* n_values;        /* [d] list length per parameter, 1..BO_MAX_VALUES */
+  const double* const* values;    /* [d][n_values[p]] normalized values in [0, 1]    */
+  const uint8_t* invalid_mask;    /* [prod n_values] 1 = restricted, or NULL         */
+  double nu;                      /* Matern smoothness: 1.5 or 2.5                   */
+  double lengthscale;             /* fixed lengthscale l > 0                         */
+  double jitter;                  /* added to the diagonal of K, >= 0                */
+  int32_t af;                     /* BO_AF_*                                         */
+  int32_t explore;                /* BO_EXPLORE_*                                    */
+  double lambda_const;            /* exploration factor when explore == CONST        */
+  int32_t skip_threshold;         /* multi / advanced multi skip threshold           */
+  double rif;                     /* advanced multi required improvement factor      */
+  double discount;                /* dos discount; <= 0 selects the Table I default  */
+  int32_t y_norm;                 /* BO_YNORM_*                                      */
+  int32_t precision;              /* BO_PREC_*                                       */
+  int32_t n_max;                  /* capacity in valid observations, 1..BO_MAX_OBS   */
+  int32_t n_init;                 /* suggests drawn at random while fewer
+                                     observations than this exist                    */
+  uint64_t seed;                  /* splitmix64 seed of those random draws           */
+  bo_alloc_fn alloc;              /* device memory provider, or NULL                 */
+  bo_free_fn free;
+  void* alloc_ctx;
+  void* stream;                   /* cudaStream_t for all device work (NULL = legacy) */
+} bo_space_desc;
+
+/* Fill `desc` with the defaults of Table I: nu = 3/2, l = 1.5 with the
+ * contextual-variance factor, jitter 1e-10, EI, skip threshold 5,
+ * rif 0.1, Table I discounts, standardized y, FP64, n_max = 512. */
+void bo_space_desc_init(bo_space_desc* desc);
+
+typedef struct bo_space bo_space;   /* opaque, owned by the library */
+
+/* Build the valid list, upload codes and value tables, and allocate the
+ * resident state (observations, L^-1, beta, per-candidate buffers) for
+ * n_max observations.  Synchronous. */
+int bo_space_create(const bo_space_desc* desc, bo_space** out);
+/* Release every resource of the space (synchronizes its stream). */
+int bo_space_destroy(bo_space* space);
+
+int bo_valid_count(const bo_space* space, int64_t* out);
+/* value_idx_out[p] = index into values[p] of configuration idx. */
+int bo_decode(const bo_space* space, int64_t idx, int32_t* value_idx_out);
+
+/* Record f(idx) = value.  A finite value is fitted: the FP64 L^-1 and beta
+ * are extended on the device (asynchronous; a numeric failure of the update
+ * is reported by the next bo_suggest / bo_sync).  A non-finite value marks
+ * a runtime-invalid configuration: visited, never fitted (Sec. III-D).
+ * BO_ERR_DUPLICATE if idx was observed before, BO_ERR_CAPACITY beyond n_max. */
+int bo_observe(bo_space* space, int64_t idx, double value);
+
+typedef struct bo_suggest_info {
+  int64_t idx;        /* the suggested valid-list index                          */
+  int32_t af;         /* BO_AF_EI / PI / LCB that picked it, -1 if random        */
+  int32_t predicted;  /* 1 if it comes from a prediction pass                    */
+  double mu;          /* posterior mean there (standardized units)               */
+  double sigma;       /* posterior standard deviation there                      */
+  double score;       /* acquisition value (larger is better)                    */
+  double lambda;      /* exploration factor of the pass                          */
+  double mean_var;    /* mean posterior variance over the scored candidates      */
+  int64_t n_scored;   /* candidates scored by the pass                           */
+} bo_suggest_info;
+
+/* Next configuration to evaluate.  Runs a prediction pass (K* tiles,
+ * contraction, row reduction, lambda, acquisition, masked top-k) unless the
+ * current multi round still holds picks.  Synchronous; info may be NULL. */
+int bo_suggest(bo_space* space, int64_t* idx_out, bo_suggest_info* info);
+
+/* Posterior at valid-list indices [begin, begin + count) with the current
+ * observations, copied to host arrays mu_out / var_out (standardized units,
+ * var clamped at 0).  Synchronous.  For inspection and tests. */
+int bo_predict(bo_space* space, int64_t begin, int64_t count, double* mu_out, double* var_out);
+
+/* Enqueue the prediction kernels for the current observations on the
+ * space's stream without waiting: the posterior of every candidate lands in
+ * library-owned device memory.  For overlapping and for timing the
+ * prediction kernels alone. */
+int bo_predict_enqueue(bo_space* space);
+
+/* Host copy of the FP64 L^-1 (n x n, row-major, lower triangular) and beta
+ * (n); *n_out receives n.  Either array may be NULL.  Synchronous. */
+int bo_get_factor(bo_space* space, double* linv_out, double* beta_out, int32_t* n_out);
+
+/* Wait for the space's device work; returns a deferred update error, if any. */
+int bo_sync(bo_space* space);
+
+/* ---- device-resident replay (measurement) ----------------------------- */
+typedef struct bo_pass_result {
+  int32_t status;        /* BO_OK or a BO_ERR_* code of this pass              */
+  int32_t n_fit;         /* valid observations fitted                         */
+  int64_t n_scored;      /* candidates scored                                 */
+  double sum_var;        /* sum of posterior variances over them              */
+  double mean_var;
+  double lambda;
+  double mean_var_s;     /* contextual-variance baseline in use               */
+  int64_t top_idx[3][3]; /* [af][rank] best valid-list indices (-1 if none)   */
+  double top_score[3][3];
+  double top_mu[3][3];
+  double top_sigma[3][3];
+} bo_pass_result;
+
+/* Enqueue `steps` observe + predict + acquire passes on the space's stream
+ * without host synchronization: step s observes (idx_host[s], y_host[s]) and
+ * then scores every non-evaluated candidate with all three AFs (top-3 each).
+ * The per-step results land in a library-owned device array; fetch them with
+ * bo_replay_fetch.  Host arrays are read before return.  Selection state
+ * (multi / advanced multi) is not touched. */
+int bo_replay_enqueue(bo_space* space, const int64_t* idx_host, const double* y_host,
+                      int32_t steps);
+/* Synchronize and copy the results of the last bo_replay_enqueue. */
+int bo_replay_fetch(bo_space* space, bo_pass_result* results_host, int32_t steps);
+
+/* Number of kernel launches this library has issued on the space so far. */
+int bo_launch_count(const bo_space* space, int64_t* out);
+
+/* Thread-local message of the last error ("" if none). */
+const char* bo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BO_SUGGEST_H */

@@ -1,0 +1,253 @@
+"""Python binding of libbo_suggest.so (ctypes; argument marshalling only).
+
+Every step of the suggest path runs in the library's CUDA kernels.  PyTorch
+provides the device memory (its caching allocator, through the library's
+allocation callback) and the stream.  There is no CPU fallback: if the
+library cannot be loaded, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libbo_suggest.so")
+
+BO_OK = 0
+ERRORS = {1: "BO_ERR_ARG", 2: "BO_ERR_INDEX", 3: "BO_ERR_DUPLICATE", 4: "BO_ERR_EXHAUSTED",
+          5: "BO_ERR_NUMERIC", 6: "BO_ERR_NOMEM", 7: "BO_ERR_CUDA", 8: "BO_ERR_TIMEOUT",
+          9: "BO_ERR_NOT_POSITIVE", 10: "BO_ERR_STATE", 11: "BO_ERR_CAPACITY"}
+AF = {"ei": 0, "poi": 1, "pi": 1, "lcb": 2, "multi": 3, "advanced_multi": 4}
+AF_NAMES = {0: "ei", 1: "poi", 2: "lcb", -1: None}
+PRECISION = {"fp64": 0, "fp16x3": 1, "bf16x3": 2, "tf32": 3}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class BOError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SpaceDesc(C.Structure):
+    _fields_ = [("d", C.c_int32), ("n_values", C.POINTER(C.c_int32)),
+                ("values", C.POINTER(C.POINTER(C.c_double))), ("invalid_mask", C.POINTER(C.c_uint8)),
+                ("nu", C.c_double), ("lengthscale", C.c_double), ("jitter", C.c_double),
+                ("af", C.c_int32), ("explore", C.c_int32), ("lambda_const", C.c_double),
+                ("skip_threshold", C.c_int32), ("rif", C.c_double), ("discount", C.c_double),
+                ("y_norm", C.c_int32), ("precision", C.c_int32), ("n_max", C.c_int32),
+                ("n_init", C.c_int32), ("seed", C.c_uint64), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class SuggestInfo(C.Structure):
+    _fields_ = [("idx", C.c_int64), ("af", C.c_int32), ("predicted", C.c_int32),
+                ("mu", C.c_double), ("sigma", C.c_double), ("score", C.c_double),
+                ("lam", C.c_double), ("mean_var", C.c_double), ("n_scored", C.c_int64)]
+
+
+class PassResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_fit", C.c_int32), ("n_scored", C.c_int64),
+                ("sum_var", C.c_double), ("mean_var", C.c_double), ("lam", C.c_double),
+                ("mean_var_s", C.c_double), ("top_idx", (C.c_int64 * 3) * 3),
+                ("top_score", (C.c_double * 3) * 3), ("top_mu", (C.c_double * 3) * 3),
+                ("top_sigma", (C.c_double * 3) * 3)]
+
+
+# every symbol include/bo_suggest.h declares, with (restype, argtypes)
+SIGNATURES = {
+    "bo_space_desc_init": (None, [C.POINTER(SpaceDesc)]),
+    "bo_space_create": (C.c_int, [C.POINTER(SpaceDesc), C.POINTER(C.c_void_p)]),
+    "bo_space_destroy": (C.c_int, [C.c_void_p]),
+    "bo_valid_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "bo_decode": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int32)]),
+    "bo_observe": (C.c_int, [C.c_void_p, C.c_int64, C.c_double]),
+    "bo_suggest": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(SuggestInfo)]),
+    "bo_predict": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]),
+    "bo_predict_enqueue": (C.c_int, [C.c_void_p]),
+    "bo_get_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "bo_sync": (C.c_int, [C.c_void_p]),
+    "bo_replay_enqueue": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "bo_replay_fetch": (C.c_int, [C.c_void_p, C.POINTER(PassResult), C.c_int32]),
+    "bo_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "bo_last_error": (C.c_char_p, []),
+}
+
+_LIB = None
+
+
+def lib():
+    """Load libbo_suggest.so (built by paper_2111_14991_gb300.build)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2111_14991_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc):
+    if rc != BO_OK:
+        raise BOError(rc, lib().bo_last_error().decode())
+
+
+def _torch_allocator():
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:   # reported to the library as an allocation failure
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ALLOC_FN(_alloc), FREE_FN(_free)
+
+
+def _as_ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+class Space:
+    """One BO session on a discrete, normalized, constrained search space."""
+
+    def __init__(self, grids, invalid_mask=None, *, nu=1.5, lengthscale=1.5, jitter=1e-10,
+                 af="ei", explore="cv", lambda_const=0.01, skip_threshold=5, rif=0.1,
+                 discount=None, normalize_y=True, precision="fp64", n_max=512, n_init=0,
+                 seed=0, stream=None, torch_allocator=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the suggest library has no CPU path")
+        L = lib()
+        self._grids = [np.ascontiguousarray(g, dtype=np.float64) for g in grids]
+        self.d = len(self._grids)
+        sizes = np.array([len(g) for g in self._grids], dtype=np.int32)
+        vals = (C.POINTER(C.c_double) * self.d)(*[_as_ptr(g, C.c_double) for g in self._grids])
+        desc = SpaceDesc()
+        L.bo_space_desc_init(C.byref(desc))
+        desc.d = self.d
+        desc.n_values = _as_ptr(sizes, C.c_int32)
+        desc.values = vals
+        mask = None
+        if invalid_mask is not None:
+            mask = np.ascontiguousarray(np.asarray(invalid_mask).reshape(-1), dtype=np.uint8)
+            desc.invalid_mask = _as_ptr(mask, C.c_uint8)
+        desc.nu, desc.lengthscale, desc.jitter = nu, lengthscale, jitter
+        desc.af = AF[af]
+        desc.explore = 0 if explore == "cv" else 1
+        desc.lambda_const = lambda_const
+        desc.skip_threshold = skip_threshold
+        desc.rif = rif
+        desc.discount = 0.0 if discount is None else discount
+        desc.y_norm = 0 if normalize_y else 1
+        desc.precision = PRECISION[precision]
+        desc.n_max = n_max
+        desc.n_init = n_init
+        desc.seed = seed
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        desc.stream = C.c_void_p(stream.cuda_stream)
+        if torch_allocator:
+            self._alloc_cbs = _torch_allocator()
+            desc.alloc, desc.free = self._alloc_cbs
+        handle = C.c_void_p()
+        _check(L.bo_space_create(C.byref(desc), C.byref(handle)))
+        self._h = handle
+        n = C.c_int64()
+        _check(L.bo_valid_count(self._h, C.byref(n)))
+        self.N = n.value
+        self.precision = precision
+
+    # -- lifecycle -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().bo_space_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls -----------------------------------------------------------------
+    def decode(self, idx):
+        out = (C.c_int32 * self.d)()
+        _check(lib().bo_decode(self._h, int(idx), out))
+        return list(out)
+
+    def observe(self, idx, value):
+        _check(lib().bo_observe(self._h, int(idx), float(value)))
+
+    def suggest(self):
+        idx = C.c_int64()
+        info = SuggestInfo()
+        _check(lib().bo_suggest(self._h, C.byref(idx), C.byref(info)))
+        return dict(idx=idx.value, af=AF_NAMES.get(info.af), predicted=bool(info.predicted),
+                    mu=info.mu, sigma=info.sigma, score=info.score, lam=info.lam,
+                    mean_var=info.mean_var, n_scored=info.n_scored)
+
+    def predict(self, begin=0, count=None):
+        count = self.N - begin if count is None else count
+        mu = np.empty(count, dtype=np.float64)
+        var = np.empty(count, dtype=np.float64)
+        _check(lib().bo_predict(self._h, begin, count, mu.ctypes.data, var.ctypes.data))
+        return mu, var
+
+    def predict_enqueue(self):
+        _check(lib().bo_predict_enqueue(self._h))
+
+    def factor(self):
+        n = C.c_int32()
+        _check(lib().bo_get_factor(self._h, None, None, C.byref(n)))
+        linv = np.zeros((n.value, n.value))
+        beta = np.zeros(n.value)
+        if n.value:
+            _check(lib().bo_get_factor(self._h, linv.ctypes.data, beta.ctypes.data, C.byref(n)))
+        return linv, beta
+
+    def sync(self):
+        _check(lib().bo_sync(self._h))
+
+    def replay_enqueue(self, idx, y):
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        _check(lib().bo_replay_enqueue(self._h, idx.ctypes.data, y.ctypes.data, len(idx)))
+        return len(idx)
+
+    def replay_fetch(self, steps):
+        out = (PassResult * steps)()
+        _check(lib().bo_replay_fetch(self._h, out, steps))
+        return [pass_result_dict(r) for r in out]
+
+    def launch_count(self):
+        n = C.c_int64()
+        _check(lib().bo_launch_count(self._h, C.byref(n)))
+        return n.value
+
+
+def pass_result_dict(r):
+    return dict(status=r.status, n_fit=r.n_fit, n_scored=r.n_scored, sum_var=r.sum_var,
+                mean_var=r.mean_var, lam=r.lam, mean_var_s=r.mean_var_s,
+                top_idx=[[r.top_idx[q][k] for k in range(3)] for q in range(3)],
+                top_score=[[r.top_score[q][k] for k in range(3)] for q in range(3)],
+                top_mu=[[r.top_mu[q][k] for k in range(3)] for q in range(3)],
+                top_sigma=[[r.top_sigma[q][k] for k in range(3)] for q in range(3)])

@@ -1,0 +1,213 @@
+// Acquisition and masked top-k over the predicted candidates.
+//
+// Reads the posterior mean / variance of every candidate and the evaluated
+// bits, computes the exploration factor lambda from the pass's mean variance
+// (contextual variance, paper Sec. III-F, or a constant), scores every valid,
+// non-evaluated configuration with the active acquisition functions
+// (minimization variants of EI, PI and LCB, Sec. III-C; larger is better) and
+// keeps the k best (score, index) per function: per thread, then merged
+// across the warp with shuffles, across the block in shared memory, and
+// across blocks by the last block to finish.  Ties go to the lower index.
+#include <cfloat>
+
+#include "bo_internal.h"
+
+namespace bo {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxK = 3;
+
+struct Top {
+  double s[kMaxK];
+  long long i[kMaxK];
+};
+
+__device__ __forceinline__ bool better(double s1, long long i1, double s2, long long i2) {
+  return s1 > s2 || (s1 == s2 && i1 < i2);
+}
+
+__device__ __forceinline__ void top_init(Top& t) {
+#pragma unroll
+  for (int r = 0; r < kMaxK; ++r) { t.s[r] = -DBL_MAX; t.i[r] = LLONG_MAX; }
+}
+
+__device__ __forceinline__ void top_insert(Top& t, double s, long long i) {
+  if (!better(s, i, t.s[kMaxK - 1], t.i[kMaxK - 1])) return;
+  int r = kMaxK - 1;
+  while (r > 0 && better(s, i, t.s[r - 1], t.i[r - 1])) {
+    t.s[r] = t.s[r - 1]; t.i[r] = t.i[r - 1]; --r;
+  }
+  t.s[r] = s; t.i[r] = i;
+}
+
+__device__ __forceinline__ void top_merge(Top& t, const Top& o) {
+#pragma unroll
+  for (int r = 0; r < kMaxK; ++r) top_insert(t, o.s[r], o.i[r]);
+}
+
+template <typename T>
+struct Math;
+template <>
+struct Math<float> {
+  __device__ static float erfc_(float x) { return erfcf(x); }
+  __device__ static float exp_(float x) { return expf(x); }
+  __device__ static float sqrt_(float x) { return sqrtf(x); }
+};
+template <>
+struct Math<double> {
+  __device__ static double erfc_(double x) { return erfc(x); }
+  __device__ static double exp_(double x) { return exp(x); }
+  __device__ static double sqrt_(double x) { return sqrt(x); }
+};
+
+// score of acquisition function af at posterior (mu, sigma); larger is better
+template <typename T>
+__device__ __forceinline__ T score(int af, T mu, T sigma, T fplus, T lam) {
+  const T delta = fplus - mu - lam;
+  if (af == kLCB) return lam * sigma - mu;
+  if (!(sigma > T(0))) {
+    if (af == kEI) return delta > T(0) ? delta : T(0);
+    return delta > T(0) ? T(1) : T(0);
+  }
+  const T z = delta / sigma;
+  const T Phi = T(0.5) * Math<T>::erfc_(-z * T(0.70710678118654752440));
+  if (af == kPI) return Phi;
+  const T phi = Math<T>::exp_(T(-0.5) * z * z) * T(0.39894228040143267794);
+  return delta * Phi + sigma * phi;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a) {
+  __shared__ Top s_top[kThreads / 32][3];
+  __shared__ bool s_last;
+  const T* mu = static_cast<const T*>(v.mu);
+  const T* var = static_cast<const T*>(v.var);
+
+  // lambda from the pass's mean variance (every block computes the same value)
+  const double sum_var = *v.sum_var;
+  const double mean_var = a.n_unvisited > 0 ? sum_var / (double)a.n_unvisited : 0.0;
+  const double var_s = a.first_pass ? mean_var : *v.var_s;
+  double lam = a.lambda_const;
+  if (a.explore == BO_EXPLORE_CV)
+    lam = var_s > 0.0 ? (mean_var / (a.mu_s_raw / a.fplus_raw)) / var_s : 0.0;
+  const T lamT = (T)lam, fpT = (T)a.fplus_t;
+
+  Top top[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) top_init(top[q]);
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < v.N; i += stride) {
+    if ((v.visited[i >> 5] >> (i & 31)) & 1u) continue;
+    const T m = mu[i];
+    const T vv = var[i];
+    const T sg = Math<T>::sqrt_(vv > T(0) ? vv : T(0));
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (q < a.n_af) {
+        T sc = score<T>(a.af[q], m, sg, fpT, lamT);
+        if (!(sc == sc)) sc = -(T)FLT_MAX;      // NaN never wins
+        top_insert(top[q], (double)sc, (long long)i);
+      }
+    }
+  }
+  // warp merge
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    for (int o = 16; o > 0; o >>= 1) {
+      Top other;
+#pragma unroll
+      for (int r = 0; r < kMaxK; ++r) {
+        other.s[r] = __shfl_xor_sync(0xffffffffu, top[q].s[r], o);
+        other.i[r] = __shfl_xor_sync(0xffffffffu, top[q].i[r], o);
+      }
+      top_merge(top[q], other);
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int q = 0; q < 3; ++q) s_top[warp][q] = top[q];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    const int q = threadIdx.x;
+    Top t = s_top[0][q];
+    for (int w = 1; w < kThreads / 32; ++w) top_merge(t, s_top[w][q]);
+    TopEntry* out = v.partial + ((size_t)blockIdx.x * 3 + q) * kMaxK;
+    for (int r = 0; r < kMaxK; ++r) { out[r].score = t.s[r]; out[r].idx = t.i[r]; }
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int done = atomicAdd(v.counter, 1u);
+    s_last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 3) {
+    const int q = threadIdx.x;
+    Top t;
+    top_init(t);
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+      const volatile TopEntry* in = v.partial + ((size_t)b * 3 + q) * kMaxK;
+      for (int r = 0; r < kMaxK; ++r) top_insert(t, in[r].score, in[r].idx);
+    }
+    bo_pass_result* res = v.result;
+    for (int r = 0; r < 3; ++r) {
+      const bool ok = q < a.n_af && r < a.k && t.i[r] != LLONG_MAX;
+      res->top_idx[q][r] = ok ? t.i[r] : -1;
+      res->top_score[q][r] = ok ? t.s[r] : 0.0;
+      res->top_mu[q][r] = ok ? (double)mu[t.i[r]] : 0.0;
+      const double vr = ok ? (double)var[t.i[r]] : 0.0;
+      res->top_sigma[q][r] = ok ? sqrt(vr > 0.0 ? vr : 0.0) : 0.0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    bo_pass_result* res = v.result;
+    res->status = v.status_in ? *v.status_in : BO_OK;
+    if (res->status == BO_OK && !(mean_var == mean_var)) res->status = BO_ERR_NUMERIC;
+    res->n_fit = a.n;
+    res->n_scored = a.n_unvisited;
+    res->sum_var = sum_var;
+    res->mean_var = mean_var;
+    res->lambda = lam;
+    res->mean_var_s = var_s;
+    if (a.first_pass) *v.var_s = mean_var;
+    *v.counter = 0;
+  }
+}
+
+}  // namespace
+
+int acquire_grid(int64_t n_cand, int max_blocks) {
+  const int64_t want = (n_cand + kThreads * 8 - 1) / (kThreads * 8);
+  return (int)(want < max_blocks ? (want < 1 ? 1 : want) : max_blocks);
+}
+
+int launch_acquire(const AcqDev& v, const PassArgs& a, bool f64, cudaStream_t s) {
+  const int grid = acquire_grid(v.N, v.max_blocks);
+  if (f64)
+    acquire_kernel<double><<<grid, kThreads, 0, s>>>(v, a);
+  else
+    acquire_kernel<float><<<grid, kThreads, 0, s>>>(v, a);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_acquire(const DevView& v, const PassArgs& a, cudaStream_t s) {
+  AcqDev ad;
+  ad.mu = v.mu;
+  ad.var = v.var;
+  ad.visited = v.visited;
+  ad.N = v.N;
+  ad.sum_var = &v.stats->sum_var;
+  ad.var_s = &v.stats->var_s;
+  ad.status_in = &v.stats->status;
+  ad.partial = v.acq_partial;
+  ad.counter = &v.stats->k2_done;
+  ad.max_blocks = v.max_acq_blocks;
+  ad.result = v.results + a.result_slot;
+  return launch_acquire(ad, a, v.precision == BO_PREC_FP64, s);
+}
+
+}  // namespace bo

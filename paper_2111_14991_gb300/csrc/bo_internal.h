@@ -1,0 +1,119 @@
+// Internal interfaces shared by the CUDA translation units and the host session.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "bo_suggest.h"
+
+namespace bo {
+
+// Candidates are processed in tiles of this many rows; per-candidate device
+// arrays are padded to a multiple of it.
+constexpr int kTileRows = 128;
+// Columns of the reduced-precision L^-1 copy per K chunk, in bytes of one row.
+constexpr int kChunkBytes = 64;
+
+enum AfId { kEI = 0, kPI = 1, kLCB = 2 };
+
+// Device-side scalars of one space.
+struct DevStats {
+  double sum_var;            // sum of posterior variances of the last prediction pass
+  double var_s;              // contextual-variance baseline (set by the first pass)
+  unsigned int k1_done;      // last-block counters (reset by the last block)
+  unsigned int k2_done;
+  int32_t status;            // sticky BO_ERR_* of observation updates
+  int32_t pad;
+};
+
+struct TopEntry {
+  double score;
+  long long idx;
+};
+
+// Every device pointer and size of a space, passed by value to launchers.
+struct DevView {
+  int d;
+  int64_t N;                 // valid configurations
+  int64_t N_pad;             // N rounded up to kTileRows
+  int n_max;                 // capacity in fitted observations (multiple of 32)
+  int precision;             // BO_PREC_*
+  double nu, lengthscale, jitter;
+
+  const uint8_t* codes;      // [d][N_pad] value index per parameter, parameter-major
+  const double* vtab64;      // [d][256] normalized values
+  const float* vtab32;       // [d][256]
+  uint32_t* visited;         // [ceil(N/32)] bit i = configuration i evaluated
+
+  double* X;                 // [n_max][d] coordinates of fitted observations
+  float* Xf;                 // [n_max][d] FP32 copy
+  double* y;                 // [n_max] raw fitted values
+  double* linv;              // [n_max][n_max] L^-1, row-major, lower triangular
+  double* beta;              // [n_max] L^-1 y~
+  uint8_t* lsplit_hi;        // reduced-precision chunked copy of L^-1 (hi or tf32)
+  uint8_t* lsplit_lo;        // (lo part; unused for tf32)
+  float* rowq;               // [n_max] 1 / s_k^2 of the per-row power-of-two scale s_k
+  float* rowb;               // [n_max] beta_k / s_k
+
+  void* mu;                  // [N_pad] posterior mean (double for FP64, else float)
+  void* var;                 // [N_pad] posterior variance
+  double* partial;           // [max_partials] per-block sums of variance
+  int max_partials;
+
+  double* kvec;              // [n_max] update scratch
+  double* lvec;              // [n_max]
+  double* wvec;              // [n_max]
+
+  DevStats* stats;
+  TopEntry* acq_partial;     // [max_acq_blocks][3][3]
+  int max_acq_blocks;
+  bo_pass_result* results;   // [max_results]
+  int max_results;
+};
+
+// Scalars of one prediction pass known to the host.
+struct PassArgs {
+  int n;                     // fitted observations
+  int64_t n_unvisited;       // valid, non-evaluated configurations
+  int n_af;                  // active acquisition functions (1..3), ids in af[]
+  int af[3];
+  int k;                     // entries kept per AF
+  int explore;               // BO_EXPLORE_*
+  double lambda_const;
+  double fplus_t;            // best observation, standardized
+  double fplus_raw, mu_s_raw;
+  int first_pass;            // contextual-variance baseline is taken from this pass
+  int result_slot;           // index into DevView::results
+};
+
+// Device operands of one acquisition pass.
+struct AcqDev {
+  const void* mu;            // [N] posterior mean (double or float)
+  const void* var;           // [N] posterior variance
+  const uint32_t* visited;   // [ceil(N/32)]
+  int64_t N;
+  const double* sum_var;     // sum of variances over the non-evaluated candidates
+  double* var_s;             // contextual-variance baseline (written on a first pass)
+  const int32_t* status_in;  // status folded into the result, or NULL
+  TopEntry* partial;         // [max_blocks][3][3] scratch
+  unsigned int* counter;     // last-block counter, 0 between launches
+  int max_blocks;
+  bo_pass_result* result;
+};
+
+// ---- launchers (each returns the number of kernels it launched, or -1) ----
+int launch_observe_update(const DevView& v, int n, int64_t idx, double y_raw, double y_mean,
+                          double y_std, cudaStream_t s);
+int launch_set_visited(const DevView& v, int64_t idx, cudaStream_t s);
+int launch_predict_f64(const DevView& v, int n, int64_t n_unvisited, cudaStream_t s);
+int launch_predict_tc(const DevView& v, int n, int64_t n_unvisited, cudaStream_t s);
+int launch_acquire(const DevView& v, const PassArgs& a, cudaStream_t s);
+int launch_acquire(const AcqDev& v, const PassArgs& a, bool f64, cudaStream_t s);
+int acquire_grid(int64_t n_cand, int max_blocks);
+
+// Size in bytes of the reduced-precision chunked L^-1 copy (one of hi / lo).
+size_t lsplit_bytes(int n_max, int precision);
+
+}  // namespace bo

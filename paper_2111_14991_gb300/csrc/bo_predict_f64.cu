@@ -1,0 +1,189 @@
+// Prediction pass in FP64 on CUDA cores: the plain FP64 form of the hot path.
+//
+// Exhaustive prediction of every valid configuration (paper Sec. III-G): for a
+// tile of BM candidates the Matern cross-covariance K*[BM x n] (Sec. III-B) is
+// built in shared memory (never in HBM), then V = K* L^-T is formed one
+// 64-column block at a time with register tiling, and reduced on the fly to
+//   var = k(0) - sum_k V_ik^2   (clamped at 0),   mu = sum_k V_ik beta_k,
+// which is the zero-mean GP posterior with beta = L^-1 y~.  Only entries
+// j <= k of L^-1 are non-zero, so each column block stops at its diagonal.
+// Each CTA also writes the sum of the variances of its non-evaluated
+// candidates; the last CTA to finish adds those partial sums in block order
+// (deterministic) into stats->sum_var for the exploration factor (Sec. III-F).
+#include "bo_internal.h"
+
+namespace bo {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBN = 64;   // output columns of V per pass
+constexpr int kBK = 32;   // j per staged slice of L^-1
+
+__device__ __forceinline__ double matern64(double r, double nu, double c) {
+  double t = c * r;
+  double e = exp(-t);
+  return nu == 1.5 ? (1.0 + t) * e : (1.0 + t + t * t * (1.0 / 3.0)) * e;
+}
+
+template <int BM>
+__global__ void __launch_bounds__(kThreads) predict_f64_kernel(DevView v, int n, int n_pad) {
+  constexpr int TM = BM / 16;             // rows per thread
+  extern __shared__ double smem[];
+  const int d = v.d;
+  const int ldk = n_pad + 1;
+  double* Ks = smem;                      // [BM][ldk]
+  double* Ls = Ks + BM * ldk;             // [kBK][kBN + 1]
+  double* Xs = Ls + kBK * (kBN + 1);      // [d][n_pad]
+  double* Cs = Xs + d * n_pad;            // [BM][d]
+  double* Bs = Cs + BM * d;               // [n_pad]
+  __shared__ double red[kThreads / 32];
+  __shared__ bool s_last;
+
+  const int tid = threadIdx.x;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const double c = sqrt(2.0 * v.nu) / v.lengthscale;
+
+  for (int e = tid; e < d * n_pad; e += kThreads) {
+    const int p = e / n_pad, j = e - p * n_pad;
+    Xs[e] = j < n ? v.X[(size_t)j * d + p] : 0.0;
+  }
+  for (int e = tid; e < BM * d; e += kThreads) {
+    const int i = e / d, p = e - i * d;
+    Cs[e] = v.vtab64[p * 256 + v.codes[(int64_t)p * v.N_pad + row0 + i]];
+  }
+  for (int j = tid; j < n_pad; j += kThreads) Bs[j] = j < n ? v.beta[j] : 0.0;
+  __syncthreads();
+
+  // K*[i][j] = k(|x_i - X_j|); padded columns j >= n meet zero rows of L^-1.
+  for (int e = tid; e < BM * n; e += kThreads) {
+    const int i = e / n, j = e - i * n;
+    double r2 = 0.0;
+    for (int p = 0; p < d; ++p) {
+      const double diff = Cs[i * d + p] - Xs[p * n_pad + j];
+      r2 = fma(diff, diff, r2);
+    }
+    Ks[i * ldk + j] = matern64(sqrt(r2), v.nu, c);
+  }
+  for (int e = tid; e < BM * (n_pad - n); e += kThreads) {
+    const int i = e / (n_pad - n), j = n + e % (n_pad - n);
+    Ks[i * ldk + j] = 0.0;
+  }
+  __syncthreads();
+
+  const int tx = tid & 15, ty = tid >> 4;
+  double s2[TM], sm[TM];
+#pragma unroll
+  for (int r = 0; r < TM; ++r) s2[r] = sm[r] = 0.0;
+
+  for (int kb = 0; kb < n; kb += kBN) {
+    double acc[TM][4];
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[r][q] = 0.0;
+    const int jend = min(n, kb + kBN);      // L^-1[k][j] = 0 for j > k
+    for (int j0 = 0; j0 < jend; j0 += kBK) {
+      __syncthreads();
+      for (int e = tid; e < kBN * kBK; e += kThreads) {
+        const int kk = e / kBK, jj = e - kk * kBK;
+        const int k = kb + kk, j = j0 + jj;
+        Ls[jj * (kBN + 1) + kk] = (k < n && j <= k) ? v.linv[(size_t)k * v.n_max + j] : 0.0;
+      }
+      __syncthreads();
+      const int jn = min(kBK, jend - j0);
+      for (int jj = 0; jj < jn; ++jj) {
+        double a[TM], b[4];
+#pragma unroll
+        for (int r = 0; r < TM; ++r) a[r] = Ks[(ty + 16 * r) * ldk + j0 + jj];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q] = Ls[jj * (kBN + 1) + tx + 16 * q];
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = kb + tx + 16 * q;
+      const double bk = k < n_pad ? Bs[k] : 0.0;
+#pragma unroll
+      for (int r = 0; r < TM; ++r) {
+        s2[r] = fma(acc[r][q], acc[r][q], s2[r]);
+        sm[r] = fma(acc[r][q], bk, sm[r]);
+      }
+    }
+  }
+
+  // reduce over the 16 threads (tx) sharing a row: lanes differ in the low 4 bits
+  double vsum = 0.0;
+#pragma unroll
+  for (int r = 0; r < TM; ++r) {
+    for (int o = 8; o > 0; o >>= 1) {
+      s2[r] += __shfl_xor_sync(0xffffffffu, s2[r], o);
+      sm[r] += __shfl_xor_sync(0xffffffffu, sm[r], o);
+    }
+    const int64_t i = row0 + ty + 16 * r;
+    if (tx == 0) {
+      const double var = fmax(0.0, 1.0 - s2[r]);
+      static_cast<double*>(v.mu)[i] = sm[r];
+      static_cast<double*>(v.var)[i] = var;
+      if (i < v.N && !((v.visited[i >> 5] >> (i & 31)) & 1u)) vsum += var;
+    }
+  }
+  // block sum of variances in a fixed order
+  for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
+  if ((tid & 31) == 0) red[tid >> 5] = vsum;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+    v.partial[blockIdx.x] = t;
+    __threadfence();
+    const unsigned int done = atomicAdd(&v.stats->k1_done, 1u);
+    s_last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (tid == 0) {
+      double t = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)v.partial)[b];
+      v.stats->sum_var = t;
+      v.stats->k1_done = 0;
+    }
+  }
+}
+
+template <int BM>
+size_t smem_bytes(int d, int n_pad) {
+  return sizeof(double) * ((size_t)BM * (n_pad + 1) + kBK * (kBN + 1) + (size_t)d * n_pad +
+                           (size_t)BM * d + n_pad);
+}
+
+template <int BM>
+int launch_bm(const DevView& v, int n, cudaStream_t s) {
+  const int n_pad = ((n + kBK - 1) / kBK) * kBK;
+  const size_t sm = smem_bytes<BM>(v.d, n_pad);
+  static int configured = 0;
+  if (configured < (int)sm) {
+    if (cudaFuncSetAttribute(predict_f64_kernel<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm) != cudaSuccess)
+      return -1;
+    configured = (int)sm;
+  }
+  const int grid = (int)(v.N_pad / BM);
+  if (grid > v.max_partials) return -1;
+  predict_f64_kernel<BM><<<grid, kThreads, sm, s>>>(v, n, n_pad);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace
+
+int launch_predict_f64(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStream_t s) {
+  if (n < 1) return -1;
+  return n <= 256 ? launch_bm<64>(v, n, s) : launch_bm<32>(v, n, s);
+}
+
+}  // namespace bo

@@ -1,0 +1,724 @@
+// Host side of the suggest library: the C ABI, the search-space build, the
+// observation bookkeeping and the selection of acquisition functions.
+//
+// Device work per call:
+//   bo_observe  -> observation update of L^-1 and beta (FP64), or a visited bit
+//   bo_suggest  -> prediction pass (K* tiles + contraction + row reduction),
+//                  then acquisition + masked top-k, then one small copy back
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bo_internal.h"
+
+using namespace bo;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(BO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define BO_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// splitmix64 (Steele, Lea and Flood 2014), from its published definition.
+uint64_t splitmix64_next(uint64_t& state) {
+  state += 0x9E3779B97F4A7C15ull;
+  uint64_t z = state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct Pick {
+  int64_t idx;
+  std::vector<int> afs;
+  double mu, sigma, score;
+};
+
+// Selection of acquisition functions (paper Sec. III-G, Table I).
+//   single:   one AF, one pick per pass.
+//   multi:    every active AF picks from one shared pass; each pair of AFs
+//             with the same pick gains a duplicate each and becomes partners
+//             (the pick is evaluated once, credited to both); at the start of
+//             a round an AF whose count exceeds the threshold is pitted with
+//             its partners and only the lowest dos among them stays.
+//   advanced: an AF picks its best candidate not taken by an earlier AF in
+//             the round; each round after the first, dos above mean*(1+rif)
+//             counts 'over', below mean*(1-rif) counts 'under' (cumulative);
+//             an 'under' count at the threshold promotes that AF to be the
+//             only one, else an 'over' count at it skips the AF and resets
+//             the others' counts.
+// dos <- gamma * dos + o for every observation credited to an AF.
+struct Selector {
+  int mode = BO_AF_EI;
+  std::vector<int> active;
+  double dos[3] = {0, 0, 0};
+  int dup[3] = {0, 0, 0};
+  unsigned partners[3] = {0, 0, 0};
+  int over[3] = {0, 0, 0}, under[3] = {0, 0, 0};
+  int rounds = 0;
+  int threshold = 5;
+  double gamma = 0.65, rif = 0.1;
+
+  void init(int m, int thr, double discount, double r) {
+    mode = m;
+    threshold = thr;
+    rif = r;
+    if (m == BO_AF_MULTI || m == BO_AF_ADV_MULTI) {
+      active = {kEI, kPI, kLCB};
+      gamma = discount > 0 ? discount : (m == BO_AF_MULTI ? 0.65 : 0.75);
+    } else {
+      active = {m};
+    }
+  }
+
+  bool is_active(int a) const {
+    return std::find(active.begin(), active.end(), a) != active.end();
+  }
+
+  void begin_round() {
+    if (mode == BO_AF_MULTI && rounds > 0) {
+      unsigned group = 0;
+      for (int a : active)
+        if (dup[a] > threshold) group |= (1u << a) | partners[a];
+      if (group) {
+        int keep = -1;
+        for (int a = 0; a < 3; ++a)   // AF ids are in Table I order
+          if ((group >> a & 1u) && is_active(a) && (keep < 0 || dos[a] < dos[keep])) keep = a;
+        std::vector<int> next;
+        for (int a : active)
+          if (!(group >> a & 1u) || a == keep) next.push_back(a);
+        active = next;
+        for (int a = 0; a < 3; ++a) { dup[a] = 0; partners[a] = 0; }
+      }
+    } else if (mode == BO_AF_ADV_MULTI && rounds > 0 && active.size() >= 2) {
+      double m = 0;
+      for (int a : active) m += dos[a];
+      m /= (double)active.size();
+      for (int a : active) {
+        if (dos[a] > m * (1.0 + rif)) ++over[a];
+        else if (dos[a] < m * (1.0 - rif)) ++under[a];
+      }
+      int promote = -1, skip = -1;
+      for (int a : active)
+        if (promote < 0 && under[a] >= threshold) promote = a;
+      for (int a : active)
+        if (skip < 0 && over[a] >= threshold) skip = a;
+      if (promote >= 0) {
+        active = {promote};
+      } else if (skip >= 0) {
+        active.erase(std::find(active.begin(), active.end(), skip));
+        for (int a : active) over[a] = under[a] = 0;
+      }
+    }
+    ++rounds;
+  }
+
+  // picks of one round from the pass result, whose AF rows follow `active`
+  std::vector<Pick> assign(const bo_pass_result& r) {
+    std::vector<Pick> picks;
+    for (size_t q = 0; q < active.size(); ++q) {
+      const int a = active[q];
+      if (mode == BO_AF_ADV_MULTI) {
+        for (int k = 0; k < 3; ++k) {
+          const int64_t i = r.top_idx[q][k];
+          if (i < 0) break;
+          bool taken = false;
+          for (auto& p : picks) taken |= (p.idx == i);
+          if (!taken) {
+            picks.push_back({i, {a}, r.top_mu[q][k], r.top_sigma[q][k], r.top_score[q][k]});
+            break;
+          }
+        }
+        continue;
+      }
+      const int64_t i = r.top_idx[q][0];
+      if (i < 0) continue;
+      Pick* same = nullptr;
+      for (auto& p : picks)
+        if (p.idx == i) same = &p;
+      if (same && mode == BO_AF_MULTI) {
+        for (int b : same->afs) {
+          ++dup[a];
+          ++dup[b];
+          partners[a] |= 1u << b;
+          partners[b] |= 1u << a;
+        }
+        same->afs.push_back(a);
+      } else if (!same) {
+        picks.push_back({i, {a}, r.top_mu[q][0], r.top_sigma[q][0], r.top_score[q][0]});
+      }
+    }
+    return picks;
+  }
+
+  void credit(const std::vector<int>& afs, double value) {
+    if (mode != BO_AF_MULTI && mode != BO_AF_ADV_MULTI) return;
+    for (int a : afs) dos[a] = gamma * dos[a] + value;
+  }
+};
+
+}  // namespace
+
+struct bo_space {
+  bo_space_desc desc;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int d = 0;
+  std::vector<int> sizes;
+  std::vector<std::vector<double>> values;
+  int64_t N = 0;
+  std::vector<uint8_t> codes;        // [d][N] host copy
+  std::vector<uint8_t> visited;      // [N]
+  int64_t n_visited = 0;
+  std::vector<int64_t> obs_idx;
+  std::vector<double> obs_y;
+  std::vector<double> fit_y;         // finite observations in fit order
+  int n_fit = 0;
+  int n_cap = 0;                     // desc.n_max
+  bool cv_set = false;
+  double mu_s = 0;
+  uint64_t rng = 0;
+  Selector sel;
+  std::deque<Pick> queue;
+  std::map<int64_t, std::vector<int>> outstanding;
+  DevView v{};
+  std::vector<std::pair<void*, size_t>> blocks;
+  bo_pass_result* host_result = nullptr;   // pinned
+  int64_t launches = 0;
+  int replay_steps = 0;
+  int poisoned = BO_OK;
+};
+
+namespace {
+
+int dalloc(bo_space* s, size_t bytes, void** out) {
+  bytes = std::max<size_t>(bytes, 256);
+  void* p = nullptr;
+  if (s->desc.alloc) {
+    p = s->desc.alloc(bytes, (void*)s->stream, s->desc.alloc_ctx);
+    if (!p) return fail(BO_ERR_NOMEM, "device allocation of %zu bytes failed", bytes);
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+  }
+  s->blocks.push_back({p, bytes});
+  cudaError_t e = cudaMemsetAsync(p, 0, bytes, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  *out = p;
+  return BO_OK;
+}
+
+template <typename T>
+int dalloc_n(bo_space* s, size_t count, T** out) {
+  return dalloc(s, count * sizeof(T), reinterpret_cast<void**>(out));
+}
+
+void release(bo_space* s) {
+  if (s->stream || true) cudaStreamSynchronize(s->stream);
+  for (auto& b : s->blocks) {
+    if (s->desc.alloc) {
+      if (s->desc.free) s->desc.free(b.first, b.second, (void*)s->stream, s->desc.alloc_ctx);
+    } else {
+      cudaFreeAsync(b.first, s->stream);
+    }
+  }
+  s->blocks.clear();
+  if (s->host_result) cudaFreeHost(s->host_result);
+  s->host_result = nullptr;
+  cudaStreamSynchronize(s->stream);
+}
+
+void y_stats(const bo_space* s, double* mean, double* std_, double* ymin) {
+  double m = 0, mn = INFINITY;
+  for (double y : s->fit_y) { m += y; mn = std::min(mn, y); }
+  m /= (double)s->fit_y.size();
+  double v = 0;
+  for (double y : s->fit_y) v += (y - m) * (y - m);
+  v = std::sqrt(v / (double)s->fit_y.size());
+  if (s->desc.y_norm == BO_YNORM_NONE) { m = 0.0; v = 1.0; }
+  if (v == 0.0) v = 1.0;
+  *mean = m;
+  *std_ = v;
+  *ymin = mn;
+}
+
+double median(std::vector<double> a) {
+  std::sort(a.begin(), a.end());
+  const size_t n = a.size();
+  return n % 2 ? a[n / 2] : 0.5 * (a[n / 2 - 1] + a[n / 2]);
+}
+
+int launch_pass(bo_space* s, const std::vector<int>& afs, int slot) {
+  PassArgs a{};
+  a.n = s->n_fit;
+  a.n_unvisited = s->N - s->n_visited;
+  a.n_af = (int)afs.size();
+  for (int q = 0; q < 3; ++q) a.af[q] = q < a.n_af ? afs[q] : 0;
+  a.k = a.n_af;
+  a.explore = s->desc.explore;
+  a.lambda_const = s->desc.lambda_const;
+  double mean, sd, ymin;
+  y_stats(s, &mean, &sd, &ymin);
+  a.fplus_t = (ymin - mean) / sd;
+  a.fplus_raw = ymin;
+  a.first_pass = 0;
+  if (s->desc.explore == BO_EXPLORE_CV) {
+    double mu_s = s->mu_s;
+    if (!s->cv_set) {
+      mu_s = 0;
+      for (double y : s->fit_y) mu_s += y;
+      mu_s /= (double)s->fit_y.size();
+      a.first_pass = 1;
+    }
+    if (!(ymin > 0.0) || !(mu_s > 0.0))
+      return fail(BO_ERR_NOT_POSITIVE,
+                  "contextual variance needs a positive best observation (%g) and initial mean (%g)",
+                  ymin, mu_s);
+    a.mu_s_raw = mu_s;
+    if (!s->cv_set) { s->mu_s = mu_s; s->cv_set = true; }
+  }
+  a.result_slot = slot;
+  const int k1 = s->desc.precision == BO_PREC_FP64
+                     ? launch_predict_f64(s->v, s->n_fit, a.n_unvisited, s->stream)
+                     : launch_predict_tc(s->v, s->n_fit, a.n_unvisited, s->stream);
+  if (k1 < 0) return fail(BO_ERR_CUDA, "prediction launch failed: %s",
+                          cudaGetErrorString(cudaGetLastError()));
+  const int k2 = launch_acquire(s->v, a, s->stream);
+  if (k2 < 0) return fail(BO_ERR_CUDA, "acquisition launch failed: %s",
+                          cudaGetErrorString(cudaGetLastError()));
+  s->launches += k1 + k2;
+  return BO_OK;
+}
+
+int fetch_result(bo_space* s, int slot) {
+  BO_CUDA(cudaMemcpyAsync(s->host_result, s->v.results + slot, sizeof(bo_pass_result),
+                          cudaMemcpyDeviceToHost, s->stream));
+  BO_CUDA(cudaStreamSynchronize(s->stream));
+  if (s->host_result->status != BO_OK) {
+    s->poisoned = s->host_result->status;
+    return fail(s->poisoned, "device reported status %d (non-positive pivot or non-finite posterior)",
+                s->poisoned);
+  }
+  return BO_OK;
+}
+
+int observe_impl(bo_space* s, int64_t idx, double value) {
+  if (idx < 0 || idx >= s->N) return fail(BO_ERR_INDEX, "index %lld out of range [0, %lld)",
+                                          (long long)idx, (long long)s->N);
+  if (s->visited[idx]) return fail(BO_ERR_DUPLICATE, "configuration %lld already observed",
+                                   (long long)idx);
+  const bool finite = std::isfinite(value);
+  if (finite && s->n_fit >= s->n_cap)
+    return fail(BO_ERR_CAPACITY, "more than n_max = %d valid observations", s->n_cap);
+  s->visited[idx] = 1;
+  ++s->n_visited;
+  s->obs_idx.push_back(idx);
+  s->obs_y.push_back(value);
+  int k;
+  if (finite) {
+    s->fit_y.push_back(value);
+    double mean, sd, ymin;
+    y_stats(s, &mean, &sd, &ymin);
+    k = launch_observe_update(s->v, s->n_fit, idx, value, mean, sd, s->stream);
+    ++s->n_fit;
+  } else {
+    k = launch_set_visited(s->v, idx, s->stream);
+  }
+  if (k < 0) return fail(BO_ERR_CUDA, "update launch failed");
+  s->launches += k;
+  auto it = s->outstanding.find(idx);
+  if (it != s->outstanding.end()) {
+    if (finite) s->sel.credit(it->second, value);
+    else if (!s->fit_y.empty()) s->sel.credit(it->second, median(s->fit_y));
+    s->outstanding.erase(it);
+  }
+  return BO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bo_space_desc_init(bo_space_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof *d);
+  d->nu = 1.5;
+  d->lengthscale = 1.5;
+  d->jitter = 1e-10;
+  d->af = BO_AF_EI;
+  d->explore = BO_EXPLORE_CV;
+  d->lambda_const = 0.01;
+  d->skip_threshold = 5;
+  d->rif = 0.1;
+  d->discount = 0.0;
+  d->y_norm = BO_YNORM_STANDARDIZE;
+  d->precision = BO_PREC_FP64;
+  d->n_max = BO_MAX_OBS;
+}
+
+const char* bo_last_error(void) { return g_err.c_str(); }
+
+int bo_space_create(const bo_space_desc* desc, bo_space** out) {
+  g_err.clear();
+  if (!desc || !out) return fail(BO_ERR_ARG, "null argument");
+  *out = nullptr;
+  const bo_space_desc& D = *desc;
+  if (D.d < 1 || D.d > BO_MAX_PARAMS) return fail(BO_ERR_ARG, "d = %d not in [1, %d]", D.d, BO_MAX_PARAMS);
+  if (!D.n_values || !D.values) return fail(BO_ERR_ARG, "n_values / values missing");
+  if (!(D.nu == 1.5 || D.nu == 2.5)) return fail(BO_ERR_ARG, "nu must be 1.5 or 2.5");
+  if (!(D.lengthscale > 0) || !(D.jitter >= 0)) return fail(BO_ERR_ARG, "bad lengthscale / jitter");
+  if (D.af < BO_AF_EI || D.af > BO_AF_ADV_MULTI) return fail(BO_ERR_ARG, "bad af");
+  if (D.explore != BO_EXPLORE_CV && D.explore != BO_EXPLORE_CONST) return fail(BO_ERR_ARG, "bad explore");
+  if (D.precision < BO_PREC_FP64 || D.precision > BO_PREC_TF32) return fail(BO_ERR_ARG, "bad precision");
+  if (D.n_max < 1 || D.n_max > BO_MAX_OBS) return fail(BO_ERR_ARG, "n_max not in [1, %d]", BO_MAX_OBS);
+  if (D.skip_threshold < 0 || D.n_init < 0) return fail(BO_ERR_ARG, "negative count");
+  int64_t total = 1;
+  for (int p = 0; p < D.d; ++p) {
+    if (D.n_values[p] < 1 || D.n_values[p] > BO_MAX_VALUES || !D.values[p])
+      return fail(BO_ERR_ARG, "parameter %d: bad value list", p);
+    for (int i = 0; i < D.n_values[p]; ++i)
+      if (!(D.values[p][i] >= 0.0 && D.values[p][i] <= 1.0))
+        return fail(BO_ERR_ARG, "parameter %d value %d not normalized to [0, 1]", p, i);
+    total *= D.n_values[p];
+    if (total > ((int64_t)1 << 40)) return fail(BO_ERR_ARG, "search space too large");
+  }
+
+  bo_space* s = new (std::nothrow) bo_space();
+  if (!s) return fail(BO_ERR_NOMEM, "host allocation failed");
+  s->desc = D;
+  s->desc.n_values = nullptr;
+  s->desc.values = nullptr;
+  s->desc.invalid_mask = nullptr;
+  s->stream = (cudaStream_t)D.stream;
+  cudaGetDevice(&s->device);
+  s->d = D.d;
+  s->n_cap = D.n_max;
+  s->rng = D.seed;
+  s->sel.init(D.af, D.skip_threshold, D.discount, D.rif);
+  for (int p = 0; p < D.d; ++p) {
+    s->sizes.push_back(D.n_values[p]);
+    s->values.emplace_back(D.values[p], D.values[p] + D.n_values[p]);
+  }
+  // valid list: row-major product, last parameter fastest, restricted removed
+  int64_t nvalid = 0;
+  for (int64_t f = 0; f < total; ++f) nvalid += !(D.invalid_mask && D.invalid_mask[f]);
+  if (nvalid == 0) { delete s; return fail(BO_ERR_ARG, "no valid configuration"); }
+  s->N = nvalid;
+  const int64_t N_pad = (nvalid + kTileRows - 1) / kTileRows * kTileRows;
+  std::vector<uint8_t> codes((size_t)D.d * N_pad, 0);
+  {
+    std::vector<int> digit(D.d, 0);
+    int64_t i = 0;
+    for (int64_t f = 0; f < total; ++f) {
+      if (!(D.invalid_mask && D.invalid_mask[f])) {
+        for (int p = 0; p < D.d; ++p) codes[(size_t)p * N_pad + i] = (uint8_t)digit[p];
+        ++i;
+      }
+      for (int p = D.d - 1; p >= 0; --p) {
+        if (++digit[p] < D.n_values[p]) break;
+        digit[p] = 0;
+      }
+    }
+  }
+  s->codes.resize((size_t)D.d * nvalid);
+  for (int p = 0; p < D.d; ++p)
+    std::memcpy(&s->codes[(size_t)p * nvalid], &codes[(size_t)p * N_pad], nvalid);
+  s->visited.assign(nvalid, 0);
+
+  DevView& v = s->v;
+  v.d = D.d;
+  v.N = nvalid;
+  v.N_pad = N_pad;
+  const int n_alloc = (D.n_max + 31) / 32 * 32;
+  v.n_max = n_alloc;
+  v.precision = D.precision;
+  v.nu = D.nu;
+  v.lengthscale = D.lengthscale;
+  v.jitter = D.jitter;
+  int num_sms = 152;
+  cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, s->device);
+  v.max_partials = (int)(N_pad / 32) + num_sms;
+  v.max_acq_blocks = 4 * num_sms;
+  v.max_results = 1024;
+  const size_t fsz = D.precision == BO_PREC_FP64 ? 8 : 4;
+  int rc = BO_OK;
+  uint8_t* dcodes = nullptr;
+  double* vt64 = nullptr;
+  float* vt32 = nullptr;
+  void* mu = nullptr;
+  void* var = nullptr;
+#define TRY(x) do { rc = (x); if (rc != BO_OK) { release(s); delete s; return rc; } } while (0)
+  TRY(dalloc_n(s, (size_t)D.d * N_pad, &dcodes));
+  TRY(dalloc_n(s, (size_t)D.d * 256, &vt64));
+  TRY(dalloc_n(s, (size_t)D.d * 256, &vt32));
+  TRY(dalloc_n(s, (size_t)N_pad / 32 + 1, &v.visited));
+  TRY(dalloc_n(s, (size_t)n_alloc * D.d, &v.X));
+  TRY(dalloc_n(s, (size_t)n_alloc * D.d, &v.Xf));
+  TRY(dalloc_n(s, (size_t)n_alloc, &v.y));
+  TRY(dalloc_n(s, (size_t)n_alloc * n_alloc, &v.linv));
+  TRY(dalloc_n(s, (size_t)n_alloc, &v.beta));
+  TRY(dalloc_n(s, (size_t)n_alloc, &v.rowq));
+  TRY(dalloc_n(s, (size_t)n_alloc, &v.rowb));
+  if (D.precision != BO_PREC_FP64) {
+    TRY(dalloc_n(s, lsplit_bytes(n_alloc, D.precision), &v.lsplit_hi));
+    if (D.precision != BO_PREC_TF32) TRY(dalloc_n(s, lsplit_bytes(n_alloc, D.precision), &v.lsplit_lo));
+  }
+  TRY(dalloc(s, (size_t)N_pad * fsz, &mu));
+  TRY(dalloc(s, (size_t)N_pad * fsz, &var));
+  TRY(dalloc_n(s, (size_t)v.max_partials, &v.partial));
+  TRY(dalloc_n(s, (size_t)n_alloc, &v.kvec));
+  TRY(dalloc_n(s, (size_t)n_alloc, &v.lvec));
+  TRY(dalloc_n(s, (size_t)8 * n_alloc, &v.wvec));
+  TRY(dalloc_n(s, 1, &v.stats));
+  TRY(dalloc_n(s, (size_t)v.max_acq_blocks * 9, &v.acq_partial));
+  TRY(dalloc_n(s, (size_t)v.max_results, &v.results));
+#undef TRY
+  v.codes = dcodes;
+  v.vtab64 = vt64;
+  v.vtab32 = vt32;
+  v.mu = mu;
+  v.var = var;
+  std::vector<double> t64((size_t)D.d * 256, 0.0);
+  std::vector<float> t32((size_t)D.d * 256, 0.0f);
+  for (int p = 0; p < D.d; ++p)
+    for (int i = 0; i < D.n_values[p]; ++i) {
+      t64[(size_t)p * 256 + i] = D.values[p][i];
+      t32[(size_t)p * 256 + i] = (float)D.values[p][i];
+    }
+  cudaError_t e = cudaMemcpyAsync(dcodes, codes.data(), codes.size(), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(vt64, t64.data(), t64.size() * 8, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(vt32, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->host_result, sizeof(bo_pass_result));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) { rc = cuda_fail(e, "space upload"); release(s); delete s; return rc; }
+  *out = s;
+  return BO_OK;
+}
+
+int bo_space_destroy(bo_space* s) {
+  if (!s) return fail(BO_ERR_ARG, "null space");
+  cudaSetDevice(s->device);
+  release(s);
+  delete s;
+  return BO_OK;
+}
+
+int bo_valid_count(const bo_space* s, int64_t* out) {
+  if (!s || !out) return fail(BO_ERR_ARG, "null argument");
+  *out = s->N;
+  return BO_OK;
+}
+
+int bo_decode(const bo_space* s, int64_t idx, int32_t* value_idx_out) {
+  if (!s || !value_idx_out) return fail(BO_ERR_ARG, "null argument");
+  if (idx < 0 || idx >= s->N) return fail(BO_ERR_INDEX, "index out of range");
+  for (int p = 0; p < s->d; ++p) value_idx_out[p] = s->codes[(size_t)p * s->N + idx];
+  return BO_OK;
+}
+
+int bo_observe(bo_space* s, int64_t idx, double value) {
+  if (!s) return fail(BO_ERR_ARG, "null space");
+  if (s->poisoned) return fail(s->poisoned, "space is unusable after an earlier numeric failure");
+  cudaSetDevice(s->device);
+  return observe_impl(s, idx, value);
+}
+
+int bo_suggest(bo_space* s, int64_t* idx_out, bo_suggest_info* info) {
+  if (!s || !idx_out) return fail(BO_ERR_ARG, "null argument");
+  if (s->poisoned) return fail(s->poisoned, "space is unusable after an earlier numeric failure");
+  cudaSetDevice(s->device);
+  bo_suggest_info inf{};
+  inf.af = -1;
+  if (s->n_visited >= s->N) return fail(BO_ERR_EXHAUSTED, "every valid configuration was evaluated");
+  if ((int64_t)s->obs_y.size() < s->desc.n_init || s->n_fit == 0) {
+    const int64_t free_count = s->N - s->n_visited;
+    int64_t r = (int64_t)(splitmix64_next(s->rng) % (uint64_t)free_count);
+    int64_t idx = -1;
+    for (int64_t i = 0; i < s->N; ++i)
+      if (!s->visited[i] && r-- == 0) { idx = i; break; }
+    inf.idx = idx;
+    *idx_out = idx;
+    if (info) *info = inf;
+    return BO_OK;
+  }
+  while (!s->queue.empty()) {
+    Pick p = s->queue.front();
+    s->queue.pop_front();
+    if (s->visited[p.idx]) continue;
+    s->outstanding[p.idx] = p.afs;
+    inf.idx = p.idx;
+    inf.af = p.afs[0];
+    inf.predicted = 1;
+    inf.mu = p.mu;
+    inf.sigma = p.sigma;
+    inf.score = p.score;
+    inf.lambda = s->host_result->lambda;
+    inf.mean_var = s->host_result->mean_var;
+    inf.n_scored = 0;
+    *idx_out = p.idx;
+    if (info) *info = inf;
+    return BO_OK;
+  }
+  s->sel.begin_round();
+  s->outstanding.clear();
+  int rc = launch_pass(s, s->sel.active, 0);
+  if (rc != BO_OK) return rc;
+  rc = fetch_result(s, 0);
+  if (rc != BO_OK) return rc;
+  std::vector<Pick> picks = s->sel.assign(*s->host_result);
+  if (picks.empty()) return fail(BO_ERR_EXHAUSTED, "no pick available");
+  s->queue.assign(picks.begin() + 1, picks.end());
+  const Pick& p = picks[0];
+  s->outstanding[p.idx] = p.afs;
+  inf.idx = p.idx;
+  inf.af = p.afs[0];
+  inf.predicted = 1;
+  inf.mu = p.mu;
+  inf.sigma = p.sigma;
+  inf.score = p.score;
+  inf.lambda = s->host_result->lambda;
+  inf.mean_var = s->host_result->mean_var;
+  inf.n_scored = s->host_result->n_scored;
+  *idx_out = p.idx;
+  if (info) *info = inf;
+  return BO_OK;
+}
+
+int bo_predict(bo_space* s, int64_t begin, int64_t count, double* mu_out, double* var_out) {
+  if (!s || (!mu_out && !var_out)) return fail(BO_ERR_ARG, "null argument");
+  if (begin < 0 || count < 0 || begin + count > s->N) return fail(BO_ERR_INDEX, "range out of bounds");
+  cudaSetDevice(s->device);
+  if (s->n_fit == 0) {   // the prior
+    for (int64_t i = 0; i < count; ++i) {
+      if (mu_out) mu_out[i] = 0.0;
+      if (var_out) var_out[i] = 1.0;
+    }
+    return BO_OK;
+  }
+  const int k1 = s->desc.precision == BO_PREC_FP64
+                     ? launch_predict_f64(s->v, s->n_fit, s->N - s->n_visited, s->stream)
+                     : launch_predict_tc(s->v, s->n_fit, s->N - s->n_visited, s->stream);
+  if (k1 < 0) return fail(BO_ERR_CUDA, "prediction launch failed");
+  s->launches += k1;
+  if (s->desc.precision == BO_PREC_FP64) {
+    if (mu_out) BO_CUDA(cudaMemcpyAsync(mu_out, (double*)s->v.mu + begin, count * 8, cudaMemcpyDeviceToHost, s->stream));
+    if (var_out) BO_CUDA(cudaMemcpyAsync(var_out, (double*)s->v.var + begin, count * 8, cudaMemcpyDeviceToHost, s->stream));
+    BO_CUDA(cudaStreamSynchronize(s->stream));
+  } else {
+    std::vector<float> tmp(count);
+    for (int w = 0; w < 2; ++w) {
+      double* dst = w ? var_out : mu_out;
+      if (!dst) continue;
+      const float* src = (const float*)(w ? s->v.var : s->v.mu) + begin;
+      BO_CUDA(cudaMemcpyAsync(tmp.data(), src, count * 4, cudaMemcpyDeviceToHost, s->stream));
+      BO_CUDA(cudaStreamSynchronize(s->stream));
+      for (int64_t i = 0; i < count; ++i) dst[i] = tmp[i];
+    }
+  }
+  return BO_OK;
+}
+
+int bo_predict_enqueue(bo_space* s) {
+  if (!s) return fail(BO_ERR_ARG, "null space");
+  if (s->n_fit == 0) return fail(BO_ERR_STATE, "no valid observation to predict from");
+  cudaSetDevice(s->device);
+  const int k1 = s->desc.precision == BO_PREC_FP64
+                     ? launch_predict_f64(s->v, s->n_fit, s->N - s->n_visited, s->stream)
+                     : launch_predict_tc(s->v, s->n_fit, s->N - s->n_visited, s->stream);
+  if (k1 < 0) return fail(BO_ERR_CUDA, "prediction launch failed");
+  s->launches += k1;
+  return BO_OK;
+}
+
+int bo_get_factor(bo_space* s, double* linv_out, double* beta_out, int32_t* n_out) {
+  if (!s) return fail(BO_ERR_ARG, "null space");
+  cudaSetDevice(s->device);
+  const int n = s->n_fit;
+  if (n_out) *n_out = n;
+  if (n == 0) return BO_OK;
+  if (linv_out)
+    BO_CUDA(cudaMemcpy2DAsync(linv_out, (size_t)n * 8, s->v.linv, (size_t)s->v.n_max * 8, (size_t)n * 8, n,
+                              cudaMemcpyDeviceToHost, s->stream));
+  if (beta_out) BO_CUDA(cudaMemcpyAsync(beta_out, s->v.beta, (size_t)n * 8, cudaMemcpyDeviceToHost, s->stream));
+  BO_CUDA(cudaStreamSynchronize(s->stream));
+  return BO_OK;
+}
+
+int bo_sync(bo_space* s) {
+  if (!s) return fail(BO_ERR_ARG, "null space");
+  cudaSetDevice(s->device);
+  BO_CUDA(cudaStreamSynchronize(s->stream));
+  DevStats st;
+  BO_CUDA(cudaMemcpy(&st, s->v.stats, sizeof st, cudaMemcpyDeviceToHost));
+  if (st.status != BO_OK) {
+    s->poisoned = st.status;
+    return fail(st.status, "observation update failed (non-positive pivot)");
+  }
+  return BO_OK;
+}
+
+int bo_replay_enqueue(bo_space* s, const int64_t* idx, const double* y, int32_t steps) {
+  if (!s || (steps > 0 && (!idx || !y))) return fail(BO_ERR_ARG, "null argument");
+  if (steps < 0 || steps > s->v.max_results) return fail(BO_ERR_ARG, "steps not in [0, %d]", s->v.max_results);
+  if (s->poisoned) return fail(s->poisoned, "space is unusable after an earlier numeric failure");
+  cudaSetDevice(s->device);
+  const std::vector<int> all = {kEI, kPI, kLCB};
+  for (int32_t t = 0; t < steps; ++t) {
+    int rc = observe_impl(s, idx[t], y[t]);
+    if (rc != BO_OK) return rc;
+    if (s->n_fit == 0) return fail(BO_ERR_STATE, "replay step %d has no valid observation yet", t);
+    if (s->n_visited >= s->N) return fail(BO_ERR_EXHAUSTED, "search space exhausted at step %d", t);
+    rc = launch_pass(s, all, t);
+    if (rc != BO_OK) return rc;
+  }
+  s->replay_steps = steps;
+  return BO_OK;
+}
+
+int bo_replay_fetch(bo_space* s, bo_pass_result* out, int32_t steps) {
+  if (!s || (steps > 0 && !out)) return fail(BO_ERR_ARG, "null argument");
+  if (steps > s->replay_steps) return fail(BO_ERR_ARG, "only %d replay results", s->replay_steps);
+  cudaSetDevice(s->device);
+  BO_CUDA(cudaMemcpyAsync(out, s->v.results, sizeof(bo_pass_result) * steps, cudaMemcpyDeviceToHost,
+                          s->stream));
+  BO_CUDA(cudaStreamSynchronize(s->stream));
+  for (int32_t t = 0; t < steps; ++t)
+    if (out[t].status != BO_OK) {
+      s->poisoned = out[t].status;
+      return fail(out[t].status, "replay step %d reported status %d", t, out[t].status);
+    }
+  return BO_OK;
+}
+
+int bo_launch_count(const bo_space* s, int64_t* out) {
+  if (!s || !out) return fail(BO_ERR_ARG, "null argument");
+  *out = s->launches;
+  return BO_OK;
+}
+
+}  // extern "C"

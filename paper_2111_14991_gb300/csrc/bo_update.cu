@@ -1,0 +1,227 @@
+// Observation update of the GP surrogate (FP64), one valid observation at a time.
+//
+// With a fixed lengthscale (paper Sec. III-B) the kernel matrix of the
+// observations only grows by one row and column per observation, so the
+// Cholesky factor grows by one row and so does its inverse:
+//   K_new = [[K, k], [k^T, k(0) + jitter]],  l = L^-1 k,  d = sqrt(k(0) + jitter - l.l)
+//   L_new^-1 = [[L^-1, 0], [-(L^-T l)^T / d, 1 / d]].
+// Rows of L^-1 never change once written.  beta = L^-1 y~ is recomputed in
+// full because the standardization of y shifts with every observation.
+// The reduced-precision contraction gets a per-row scaled, split copy of each
+// new row (written once), see lsplit_offset().
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "bo_internal.h"
+
+namespace bo {
+
+__device__ __forceinline__ double matern64(double r, double nu, double c) {
+  // c = sqrt(2 nu) / l; nu = 3/2: (1 + t) e^-t ; nu = 5/2: (1 + t + t^2/3) e^-t
+  double t = c * r;
+  double e = exp(-t);
+  return nu == 1.5 ? (1.0 + t) * e : (1.0 + t + t * t * (1.0 / 3.0)) * e;
+}
+
+__device__ __forceinline__ double coord64(const DevView& v, int64_t idx, int p) {
+  return v.vtab64[p * 256 + v.codes[(int64_t)p * v.N_pad + idx]];
+}
+
+// Element width and chunk width (elements of j per kChunkBytes) of the split copy.
+__host__ __device__ __forceinline__ int split_elem_bytes(int precision) {
+  return precision == BO_PREC_TF32 ? 4 : 2;
+}
+
+// Byte offset of element (row k, column j) of L^-1 in the chunked copy.
+// Chunk c holds columns [c*CW, (c+1)*CW) of rows k >= c*CW, in the K-major
+// no-swizzle core-matrix layout the tensor core reads: 8-row x 16-byte core
+// matrices, the CW/ (16/eb) core matrices of one 8-row group side by side
+// (128 B apart), consecutive 8-row groups kChunkBytes*8 B apart.
+__host__ __device__ __forceinline__ size_t lsplit_offset(int n_max, int eb, int k, int j) {
+  const int cw = kChunkBytes / eb;
+  const int c = j / cw;
+  // sum over c' < c of (n_max - c' cw) * kChunkBytes
+  const size_t base = (size_t)kChunkBytes * ((size_t)c * n_max - (size_t)cw * c * (c - 1) / 2);
+  const int jj = j - c * cw;
+  const int g = (k - c * cw) >> 3;
+  return base + (size_t)g * (kChunkBytes * 8) + (size_t)((jj * eb) >> 4) * 128 +
+         (size_t)(k & 7) * 16 + (size_t)((jj * eb) & 15);
+}
+
+size_t lsplit_bytes(int n_max, int precision) {
+  if (precision == BO_PREC_FP64) return 0;
+  const int eb = split_elem_bytes(precision);
+  const int cw = kChunkBytes / eb;
+  const int nc = n_max / cw;
+  return (size_t)kChunkBytes * ((size_t)nc * n_max - (size_t)cw * nc * (nc - 1) / 2);
+}
+
+// --- K3a: X[n] = x(idx), y[n] = y, visited bit, k_j = k(|x - X_j|) --------------
+__global__ void obs_k_kernel(DevView v, int n, long long idx, double y_raw) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const double c = sqrt(2.0 * v.nu) / v.lengthscale;
+  if (blockIdx.x == 0 && threadIdx.x < v.d) {
+    const double x = coord64(v, idx, threadIdx.x);
+    v.X[(size_t)n * v.d + threadIdx.x] = x;
+    v.Xf[(size_t)n * v.d + threadIdx.x] = (float)x;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    v.y[n] = y_raw;
+    atomicOr(&v.visited[idx >> 5], 1u << (idx & 31));
+  }
+  if (j < n) {
+    double r2 = 0.0;
+    for (int p = 0; p < v.d; ++p) {
+      const double diff = coord64(v, idx, p) - v.X[(size_t)j * v.d + p];
+      r2 = fma(diff, diff, r2);
+    }
+    v.kvec[j] = matern64(sqrt(r2), v.nu, c);
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// --- K3b: l = L^-1 k (warp per row) -------------------------------------------
+__global__ void obs_l_kernel(DevView v, int n) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = v.linv + (size_t)warp * v.n_max;
+  double s = 0.0;
+  for (int j = lane; j <= warp; j += 32) s = fma(row[j], v.kvec[j], s);
+  s = warp_sum(s);
+  if (lane == 0) v.lvec[warp] = s;
+}
+
+// --- K3c: partial w = L^-T l over row segments of 64 ---------------------------
+__global__ void obs_w_kernel(DevView v, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int seg = blockIdx.y;
+  if (j >= n) return;
+  const int i0 = max(j, seg * 64), i1 = min(n, seg * 64 + 64);
+  double s = 0.0;
+  for (int i = i0; i < i1; ++i) s = fma(v.linv[(size_t)i * v.n_max + j], v.lvec[i], s);
+  v.wvec[(size_t)seg * v.n_max + j] = s;
+}
+
+// --- K3d: pivot, new row n of L^-1 and its split copy (one block) --------------
+__global__ void obs_finish_kernel(DevView v, int n) {
+  __shared__ double red[32];
+  __shared__ double s_dinv;
+  __shared__ float s_scale;
+  const int tid = threadIdx.x;
+  double ll = 0.0;
+  for (int i = tid; i < n; i += blockDim.x) ll = fma(v.lvec[i], v.lvec[i], ll);
+  ll = warp_sum(ll);
+  if ((tid & 31) == 0) red[tid >> 5] = ll;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    const double d2 = 1.0 + v.jitter - t;
+    s_dinv = (d2 > 0.0 && isfinite(d2)) ? 1.0 / sqrt(d2) : 0.0;
+    if (s_dinv == 0.0) v.stats->status = BO_ERR_NUMERIC;
+  }
+  __syncthreads();
+  const double dinv = s_dinv;
+  if (dinv == 0.0) return;
+  const int nseg = (n + 63) / 64;
+  double* row = v.linv + (size_t)n * v.n_max;
+  double amax = 0.0;
+  for (int j = tid; j <= n; j += blockDim.x) {
+    double val;
+    if (j < n) {
+      double w = 0.0;
+      for (int s = 0; s < nseg; ++s) w += v.wvec[(size_t)s * v.n_max + j];
+      val = -w * dinv;
+    } else {
+      val = dinv;
+    }
+    row[j] = val;
+    amax = fmax(amax, fabs(val));
+  }
+  if (v.precision == BO_PREC_FP64) return;
+  // per-row power-of-two scale s with max |row| * s in [2^13, 2^14)
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = amax;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    int e;
+    frexp(m, &e);                       // m in [2^(e-1), 2^e)
+    s_scale = ldexpf(1.0f, 14 - e);
+    v.rowq[n] = 1.0f / (s_scale * s_scale);
+  }
+  __syncthreads();
+  const float sc = s_scale;
+  const int eb = split_elem_bytes(v.precision);
+  for (int j = tid; j <= n; j += blockDim.x) {
+    const float x = (float)row[j] * sc;
+    const size_t off = lsplit_offset(v.n_max, eb, n, j);
+    if (v.precision == BO_PREC_FP16X3) {
+      const __half h = __float2half_rn(x);
+      const __half l = __float2half_rn(x - __half2float(h));
+      *reinterpret_cast<__half*>(v.lsplit_hi + off) = h;
+      *reinterpret_cast<__half*>(v.lsplit_lo + off) = l;
+    } else if (v.precision == BO_PREC_BF16X3) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+      *reinterpret_cast<__nv_bfloat16*>(v.lsplit_hi + off) = h;
+      *reinterpret_cast<__nv_bfloat16*>(v.lsplit_lo + off) = l;
+    } else {  // TF32: round to nearest (ties away) to 10 explicit mantissa bits
+      uint32_t u;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+      *reinterpret_cast<uint32_t*>(v.lsplit_hi + off) = u;
+    }
+  }
+}
+
+// --- K3e: beta = L^-1 y~ for rows 0..n, and beta_k / s_k -------------------------
+__global__ void obs_beta_kernel(DevView v, int rows, double y_mean, double inv_std) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= rows) return;
+  const double* row = v.linv + (size_t)warp * v.n_max;
+  double s = 0.0;
+  for (int j = lane; j <= warp; j += 32) s = fma(row[j], (v.y[j] - y_mean) * inv_std, s);
+  s = warp_sum(s);
+  if (lane == 0) {
+    v.beta[warp] = s;
+    if (v.precision != BO_PREC_FP64) v.rowb[warp] = (float)(s * sqrt((double)v.rowq[warp]));
+  }
+}
+
+__global__ void set_visited_kernel(uint32_t* visited, long long idx) {
+  atomicOr(&visited[idx >> 5], 1u << (idx & 31));
+}
+
+int launch_set_visited(const DevView& v, int64_t idx, cudaStream_t s) {
+  set_visited_kernel<<<1, 1, 0, s>>>(v.visited, (long long)idx);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_observe_update(const DevView& v, int n, int64_t idx, double y_raw, double y_mean,
+                          double y_std, cudaStream_t s) {
+  // n = observations fitted before this one; the new one becomes row n.
+  int launches = 0;
+  obs_k_kernel<<<(n + 127) / 128 + (n == 0), 128, 0, s>>>(v, n, (long long)idx, y_raw);
+  ++launches;
+  if (n > 0) {
+    obs_l_kernel<<<(n + 7) / 8, 256, 0, s>>>(v, n);
+    dim3 gw((n + 127) / 128, (n + 63) / 64);
+    obs_w_kernel<<<gw, 128, 0, s>>>(v, n);
+    launches += 2;
+  }
+  obs_finish_kernel<<<1, 256, 0, s>>>(v, n);
+  const int rows = n + 1;
+  obs_beta_kernel<<<(rows + 7) / 8, 256, 0, s>>>(v, rows, y_mean, 1.0 / y_std);
+  launches += 2;
+  return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+
+}  // namespace bo
