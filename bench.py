@@ -122,47 +122,74 @@ def flops_per_candidate(n, d):
     return n * (n + 1) + 4 * n + n * (3 * d + 12)
 
 
-def run_ours(args, rank, world):
+def tc_mma_flops(n, N):
+    """Tensor-core flops the FP16X3 / BF16X3 kernel issues: 3 products, 32-wide
+    chunks, each chunk's N range running from its first row to n_pad."""
+    n_pad = (n + 31) // 32 * 32
+    cols = sum(n_pad - c * 32 for c in range(n_pad // 32))
+    return 3 * 2 * 128 * 32 * cols * ((N + 127) // 128)
+
+
+def roofline_for(precision, n, d, N, k1_time):
+    alg = float(N) * n * (n + 1)                       # triangular contraction, flops
+    if precision == "fp64":
+        fl = float(flops_per_candidate(n, d)) * N
+        ach = fl / k1_time / 1e12
+        tr = TRAFFIC.get("predict_f64")
+        return {"bound": "alu", "kernel": "predict_f64_kernel", "achieved": round(ach, 4),
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                "peak_source": "nominal GB300 FP64 (recipe table), not measured",
+                "traffic": tr["bytes_per_launch"] if tr and tr["src_sha"] == kernel_sha(precision) else None,
+                "flops_per_launch": fl, "launch_s": k1_time}
+    peaks = _peaks()
+    peak = peaks["bf16_tflops"] * (0.5 if precision == "tf32" else 1.0)
+    ach = alg / k1_time / 1e12
+    issued = (tc_mma_flops(n, N) / (3 if precision == "tf32" else 1)) / k1_time / 1e12
+    tr = TRAFFIC.get("predict_tc_" + precision)
+    return {"bound": "tensor", "kernel": "predict_tc_kernel<%s>" % precision, "achieved": round(ach, 2),
+            "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+            "peak_source": ("measured bf16 burst (MEASURED_PEAKS.json)" + (" x 1/2 nominal tf32 ratio"
+                            if precision == "tf32" else "; f16 runs at the bf16 rate")),
+            "mma_issued_tflops": round(issued, 1), "mma_issued_frac": round(issued / peak, 4),
+            "traffic": tr["bytes_per_launch"] if tr and tr["src_sha"] == kernel_sha(precision) else None,
+            "flops_per_launch": alg, "launch_s": k1_time}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0, "fallback": True}
+
+
+def measure_device(cfg_id, precision, steps, warm, flush, stream):
+    """Device-resident steps (observe + predict + acquire), CUDA events on the
+    session's stream, L2 flushed between steps; then the prediction kernel alone."""
     import torch
-    from paper_2111_14991_gb300 import Space, build
-    build.build()
-    dev = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(dev)
-    cfg = CONFIGS[args.config]
-    sp = space_for(args.config)
-    steps, warm = args.steps, args.warmup
+    from paper_2111_14991_gb300 import Space
+    cfg = CONFIGS[cfg_id]
+    sp = space_for(cfg_id)
     n_final = cfg["n_final"]
-    idx, y = observations(sp, args.config, n_final, seed=0)
+    idx, y = observations(sp, cfg_id, n_final, seed=0)
     n0 = max(2, n_final - steps - warm)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MB > 129 MB L2
-    stream = torch.cuda.current_stream()
-
-    def fresh():
-        s = Space(sp.grids, sp.invalid, af=cfg["af"], precision=args.precision, n_max=max(n_final, 32))
-        for i, v in zip(idx[:n0], y[:n0]):
-            s.observe(int(i), float(v))
-        s.sync()
-        return s
-
-    # ---- device-resident steps: observe + predict + acquire, events on the stream
-    s = fresh()
+    s = Space(sp.grids, sp.invalid, af=cfg["af"], precision=precision, n_max=max(n_final, 32))
+    for i, v in zip(idx[:n0], y[:n0]):
+        s.observe(int(i), float(v))
+    s.sync()
     times, scored, launches = [], 0, 0
-    with ClockSampler(dev) as clk:
-        for t in range(warm + steps):
-            j = n0 + t
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            l0 = s.launch_count()
-            e0.record(stream)
-            s.replay_enqueue([idx[j]], [y[j]])
-            e1.record(stream)
-            r = s.replay_fetch(1)[0]
-            if t >= warm:
-                times.append(e0.elapsed_time(e1) / 1e3)
-                scored += r["n_scored"]
-                launches += s.launch_count() - l0
-    clocks = clk.summary()
-    # ---- the dominant kernel alone (prediction pass) for the roofline
+    for t in range(warm + steps):
+        j = n0 + t
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = s.launch_count()
+        e0.record(stream)
+        s.replay_enqueue([idx[j]], [y[j]])
+        e1.record(stream)
+        r = s.replay_fetch(1)[0]
+        if t >= warm:
+            times.append(e0.elapsed_time(e1) / 1e3)
+            scored += r["n_scored"]
+            launches += s.launch_count() - l0
     k1 = []
     for _ in range(max(3, min(10, steps))):
         flush.zero_()
@@ -172,13 +199,34 @@ def run_ours(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         k1.append(e0.elapsed_time(e1) / 1e3)
-    n_last = n0 + warm + steps
-    N = sp.n_valid
-    k1_time = statistics.median(k1)
     s.close()
+    n_last = n0 + warm + steps
+    return dict(sp=sp, idx=idx, y=y, n0=n0, n_last=n_last, times=times, scored=scored, launches=launches,
+                k1=statistics.median(k1), value=scored / sum(times))
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2111_14991_gb300 import Space, build
+    build.build()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    cfg = CONFIGS[args.config]
+    steps, warm = args.steps, args.warmup
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    with ClockSampler(dev) as clk:
+        m = measure_device(args.config, args.precision, steps, warm, flush, stream)
+    clocks = clk.summary()
+    sp, idx, y, n0, n_last = m["sp"], m["idx"], m["y"], m["n0"], m["n_last"]
+    N = sp.n_valid
+    tot = sum(m["times"])
 
     # ---- end to end through the C ABI: observe (in) + suggest (result out), host clock
-    s = fresh()
+    s = Space(sp.grids, sp.invalid, af=cfg["af"], precision=args.precision, n_max=max(cfg["n_final"], 32))
+    for i, v in zip(idx[:n0], y[:n0]):
+        s.observe(int(i), float(v))
     for t in range(warm):
         j = n0 + t
         s.observe(int(idx[j]), float(y[j]))
@@ -191,53 +239,47 @@ def run_ours(args, rank, world):
         t0 = time.perf_counter()
         s.observe(int(idx[j]), float(y[j]))
         info = s.suggest()
-        t1 = time.perf_counter()
-        e2e_t.append(t1 - t0)
+        e2e_t.append(time.perf_counter() - t0)
         e2e_scored += info["n_scored"]
     # suggest latency at the final state (single AF: every call is a full pass)
     lat = []
-    s2 = Space(sp.grids, sp.invalid, af="ei", precision=args.precision, n_max=max(n_final, 32))
-    for i, v in zip(idx[:n_last], y[:n_last]):
-        s2.observe(int(i), float(v))
-    reps = max(args.latency_reps, steps)
-    for t in range(10 + reps):
+    for t in range(10 + max(args.latency_reps, steps)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2.suggest()
+        s.suggest()
         if t >= 10:
             lat.append(time.perf_counter() - t0)
     s.close()
-    s2.close()
-
-    # ---- aggregate over ranks: max time
-    tot = sum(times)
     e2e_tot = sum(e2e_t)
+
+    # ---- the other forms on the same GPU (device-timed, same recipe)
+    forms = {}
+    if not args.no_forms:
+        for fcfg, fprec, fsteps in ((2, "fp64", steps), (2, "fp16x3", steps), (3, "fp16x3", steps),
+                                    (3, "fp64", 3)):
+            if (fcfg, fprec) == (args.config, args.precision):
+                continue
+            f = measure_device(fcfg, fprec, fsteps, 3, flush, stream)
+            forms[f"config{fcfg}/{fprec}"] = {
+                "value": round(f["value"], 1), "unit": "candidates/s",
+                "ms_per_step": round(1e3 * sum(f["times"]) / len(f["times"]), 4),
+                "n_obs": f"{f['n0'] + 4}..{f['n_last']}",
+                "roofline": roofline_for(fprec, f["n_last"], f["sp"].d, f["sp"].n_valid, f["k1"])}
+
     if world > 1:
         import torch.distributed as dist
         tt = torch.tensor([tot, e2e_tot], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         tot, e2e_tot = tt.tolist()
-    value = scored * world / tot
+    value = m["scored"] * world / tot
     e2e_value = e2e_scored * world / e2e_tot
-    n_mid = n_last - steps // 2
-    fl = flops_per_candidate(n_last, sp.d) * N
-    achieved = fl / k1_time / 1e12
-    roofline = None
-    if args.precision == "fp64":
-        sha = kernel_sha(args.precision)
-        tr = TRAFFIC.get("predict_f64")
-        roofline = {"bound": "alu", "kernel": "predict_f64_kernel", "achieved": round(achieved, 4),
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                    "peak_source": "nominal GB300 FP64 (recipe table); no measured FP64 peak",
-                    "traffic": tr["bytes_per_launch"] if tr and tr["src_sha"] == sha else None,
-                    "flops_per_launch": fl, "launch_s": k1_time}
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "candidates/s", "n_gpus": world,
         "steps": steps, "warmup": warm, "ms_per_step": round(1e3 * tot / steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE[args.precision], "data": "synthetic (seeded landscape, clustered BO-like trace)",
-        "config": {"workload": cfg["name"], "n_obs": f"{n0 + warm + 1}..{n_last}", "n_mid": n_mid,
+        "config": {"workload": cfg["name"], "n_obs": f"{n0 + warm + 1}..{n_last}",
                    "precision": args.precision, "af_pass": "ei+poi+lcb top-3 each",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": round(1e3 * float(np.percentile(lat, 50)), 4),
@@ -245,9 +287,10 @@ def run_ours(args, rank, world):
                        "what": "bo_suggest host entry to index returned, n = %d" % n_last},
         "e2e": {"value": round(e2e_value, 1), "unit": "candidates/s", "h2d_bytes_per_step": 16,
                 "d2h_bytes_per_step": 400, "what": "bo_observe(idx, y) + bo_suggest, host clock"},
-        "gpu_launches": launches,
-        "roofline": roofline,
+        "gpu_launches": m["launches"],
+        "roofline": roofline_for(args.precision, n_last, sp.d, N, m["k1"]),
         "clocks": clocks,
+        "forms": forms,
     }
     return out
 
@@ -266,7 +309,7 @@ def cpu_baseline(cfg_id, budget_s=15.0):
     rng = np.random.default_rng(1)
     sample = min(sp.n_valid, 20000)
     done, t_pred = 0, 0.0
-    while t_pred < budget_s and done < sp.n_valid:
+    while t_pred < budget_s:
         sel = rng.choice(sp.n_valid, sample, replace=False)
         t0 = time.perf_counter()
         mu, var = O.gp_posterior(fit, coords[sel])
@@ -284,8 +327,8 @@ def cpu_baseline(cfg_id, budget_s=15.0):
         pass
     return {"value": round(done / (t_pred + t_fit * done / sp.n_valid), 1), "unit": "candidates/s",
             "cores": cores, "kind": "oracle",
-            "sample": f"{done} random candidates of {sp.n_valid} at n = {cfg['n_final']} "
-                      f"(fit once, {t_pred:.1f} s of prediction + EI/PI/LCB top-3)"}
+            "sample": f"{done} candidates in batches of {sample} drawn from the {sp.n_valid} at "
+                      f"n = {cfg['n_final']} (fit once, {t_pred:.1f} s of prediction + EI/PI/LCB top-3)"}
 
 
 def run_reference(args):
@@ -333,6 +376,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--latency-reps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", 0))

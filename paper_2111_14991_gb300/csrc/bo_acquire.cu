@@ -9,6 +9,7 @@
 // across the warp with shuffles, across the block in shared memory, and
 // across blocks by the last block to finish.  Ties go to the lower index.
 #include <cfloat>
+#include <climits>
 
 #include "bo_internal.h"
 
@@ -19,32 +20,64 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxK = 3;
 
+template <typename T>
+struct Lowest;
+template <>
+struct Lowest<float> {
+  __device__ static float v() { return -FLT_MAX; }
+};
+template <>
+struct Lowest<double> {
+  __device__ static double v() { return -DBL_MAX; }
+};
+
+template <typename T>
 struct Top {
-  double s[kMaxK];
+  T s[kMaxK];
   long long i[kMaxK];
 };
 
-__device__ __forceinline__ bool better(double s1, long long i1, double s2, long long i2) {
+template <typename T>
+__device__ __forceinline__ bool better(T s1, long long i1, T s2, long long i2) {
   return s1 > s2 || (s1 == s2 && i1 < i2);
 }
 
-__device__ __forceinline__ void top_init(Top& t) {
+template <typename T>
+__device__ __forceinline__ void top_init(Top<T>& t) {
 #pragma unroll
-  for (int r = 0; r < kMaxK; ++r) { t.s[r] = -DBL_MAX; t.i[r] = LLONG_MAX; }
+  for (int r = 0; r < kMaxK; ++r) { t.s[r] = Lowest<T>::v(); t.i[r] = LLONG_MAX; }
 }
 
-__device__ __forceinline__ void top_insert(Top& t, double s, long long i) {
+template <typename T>
+__device__ __forceinline__ void top_insert(Top<T>& t, T s, long long i) {
   if (!better(s, i, t.s[kMaxK - 1], t.i[kMaxK - 1])) return;
-  int r = kMaxK - 1;
-  while (r > 0 && better(s, i, t.s[r - 1], t.i[r - 1])) {
-    t.s[r] = t.s[r - 1]; t.i[r] = t.i[r - 1]; --r;
+  if (better(s, i, t.s[0], t.i[0])) {
+    t.s[2] = t.s[1]; t.i[2] = t.i[1]; t.s[1] = t.s[0]; t.i[1] = t.i[0]; t.s[0] = s; t.i[0] = i;
+  } else if (better(s, i, t.s[1], t.i[1])) {
+    t.s[2] = t.s[1]; t.i[2] = t.i[1]; t.s[1] = s; t.i[1] = i;
+  } else {
+    t.s[2] = s; t.i[2] = i;
   }
-  t.s[r] = s; t.i[r] = i;
 }
 
-__device__ __forceinline__ void top_merge(Top& t, const Top& o) {
+template <typename T>
+__device__ __forceinline__ void top_merge(Top<T>& t, const Top<T>& o) {
 #pragma unroll
   for (int r = 0; r < kMaxK; ++r) top_insert(t, o.s[r], o.i[r]);
+}
+
+// butterfly merge of each lane's lists across the warp
+template <typename T>
+__device__ __forceinline__ void warp_merge(Top<T>& t) {
+  for (int o = 16; o > 0; o >>= 1) {
+    Top<T> other;
+#pragma unroll
+    for (int r = 0; r < kMaxK; ++r) {
+      other.s[r] = __shfl_xor_sync(0xffffffffu, t.s[r], o);
+      other.i[r] = __shfl_xor_sync(0xffffffffu, t.i[r], o);
+    }
+    top_merge(t, other);
+  }
 }
 
 template <typename T>
@@ -80,7 +113,8 @@ __device__ __forceinline__ T score(int af, T mu, T sigma, T fplus, T lam) {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a) {
-  __shared__ Top s_top[kThreads / 32][3];
+  static_assert(kMaxK == 3, "top_insert is written for three entries");
+  __shared__ Top<T> s_top[kThreads / 32][3];
   __shared__ bool s_last;
   const T* mu = static_cast<const T*>(v.mu);
   const T* var = static_cast<const T*>(v.var);
@@ -94,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a)
     lam = var_s > 0.0 ? (mean_var / (a.mu_s_raw / a.fplus_raw)) / var_s : 0.0;
   const T lamT = (T)lam, fpT = (T)a.fplus_t;
 
-  Top top[3];
+  Top<T> top[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) top_init(top[q]);
   const int64_t stride = (int64_t)gridDim.x * kThreads;
@@ -107,34 +141,23 @@ __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a)
     for (int q = 0; q < 3; ++q) {
       if (q < a.n_af) {
         T sc = score<T>(a.af[q], m, sg, fpT, lamT);
-        if (!(sc == sc)) sc = -(T)FLT_MAX;      // NaN never wins
-        top_insert(top[q], (double)sc, (long long)i);
+        if (!(sc == sc)) sc = Lowest<T>::v() / T(2);   // NaN never wins
+        top_insert(top[q], sc, (long long)i);
       }
-    }
-  }
-  // warp merge
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    for (int o = 16; o > 0; o >>= 1) {
-      Top other;
-#pragma unroll
-      for (int r = 0; r < kMaxK; ++r) {
-        other.s[r] = __shfl_xor_sync(0xffffffffu, top[q].s[r], o);
-        other.i[r] = __shfl_xor_sync(0xffffffffu, top[q].i[r], o);
-      }
-      top_merge(top[q], other);
     }
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) warp_merge(top[q]);
   if (lane == 0)
     for (int q = 0; q < 3; ++q) s_top[warp][q] = top[q];
   __syncthreads();
   if (threadIdx.x < 3) {
     const int q = threadIdx.x;
-    Top t = s_top[0][q];
+    Top<T> t = s_top[0][q];
     for (int w = 1; w < kThreads / 32; ++w) top_merge(t, s_top[w][q]);
     TopEntry* out = v.partial + ((size_t)blockIdx.x * 3 + q) * kMaxK;
-    for (int r = 0; r < kMaxK; ++r) { out[r].score = t.s[r]; out[r].idx = t.i[r]; }
+    for (int r = 0; r < kMaxK; ++r) { out[r].score = (double)t.s[r]; out[r].idx = t.i[r]; }
     __threadfence();
   }
   __syncthreads();
@@ -145,19 +168,34 @@ __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a)
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  // last block: every thread merges a strided slice of the block partials, then
+  // warp and block merges as above (the (score, index) order is total, so the
+  // result does not depend on the merge order)
+  Top<T> fin[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) top_init(fin[q]);
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += kThreads)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const volatile TopEntry* in = v.partial + ((size_t)b * 3 + q) * kMaxK;
+#pragma unroll
+      for (int r = 0; r < kMaxK; ++r) top_insert(fin[q], (T)in[r].score, (long long)in[r].idx);
+    }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) warp_merge(fin[q]);
+  __syncthreads();
+  if (lane == 0)
+    for (int q = 0; q < 3; ++q) s_top[warp][q] = fin[q];
+  __syncthreads();
   if (threadIdx.x < 3) {
     const int q = threadIdx.x;
-    Top t;
-    top_init(t);
-    for (unsigned b = 0; b < gridDim.x; ++b) {
-      const volatile TopEntry* in = v.partial + ((size_t)b * 3 + q) * kMaxK;
-      for (int r = 0; r < kMaxK; ++r) top_insert(t, in[r].score, in[r].idx);
-    }
+    Top<T> t = s_top[0][q];
+    for (int w = 1; w < kThreads / 32; ++w) top_merge(t, s_top[w][q]);
     bo_pass_result* res = v.result;
     for (int r = 0; r < 3; ++r) {
       const bool ok = q < a.n_af && r < a.k && t.i[r] != LLONG_MAX;
       res->top_idx[q][r] = ok ? t.i[r] : -1;
-      res->top_score[q][r] = ok ? t.s[r] : 0.0;
+      res->top_score[q][r] = ok ? (double)t.s[r] : 0.0;
       res->top_mu[q][r] = ok ? (double)mu[t.i[r]] : 0.0;
       const double vr = ok ? (double)var[t.i[r]] : 0.0;
       res->top_sigma[q][r] = ok ? sqrt(vr > 0.0 ? vr : 0.0) : 0.0;
@@ -181,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a)
 }  // namespace
 
 int acquire_grid(int64_t n_cand, int max_blocks) {
-  const int64_t want = (n_cand + kThreads * 8 - 1) / (kThreads * 8);
+  const int64_t want = (n_cand + kThreads * 16 - 1) / (kThreads * 16);
   return (int)(want < max_blocks ? (want < 1 ? 1 : want) : max_blocks);
 }
 

@@ -44,11 +44,11 @@ struct DevView {
 
   const uint8_t* codes;      // [d][N_pad] value index per parameter, parameter-major
   const double* vtab64;      // [d][256] normalized values
-  const float* vtab32;       // [d][256]
+  const float* vtab32;       // [d][256] values times sqrt(2 nu) / l * log2(e), rounded once
   uint32_t* visited;         // [ceil(N/32)] bit i = configuration i evaluated
 
   double* X;                 // [n_max][d] coordinates of fitted observations
-  float* Xf;                 // [n_max][d] FP32 copy
+  float* Xf;                 // [n_max][d] FP32 copy, scaled as vtab32
   double* y;                 // [n_max] raw fitted values
   double* linv;              // [n_max][n_max] L^-1, row-major, lower triangular
   double* beta;              // [n_max] L^-1 y~
@@ -112,6 +112,12 @@ int launch_predict_tc(const DevView& v, int n, int64_t n_unvisited, cudaStream_t
 int launch_acquire(const DevView& v, const PassArgs& a, cudaStream_t s);
 int launch_acquire(const AcqDev& v, const PassArgs& a, bool f64, cudaStream_t s);
 int acquire_grid(int64_t n_cand, int max_blocks);
+
+// Scale of the FP32 coordinate copies: distances in these units are
+// u = sqrt(2 nu) r / l * log2(e), so e^-t = 2^-u with t = sqrt(2 nu) r / l.
+inline double coord_scale(double nu, double lengthscale) {
+  return 1.4426950408889634 * __builtin_sqrt(2.0 * nu) / lengthscale;
+}
 
 // Size in bytes of the reduced-precision chunked L^-1 copy (one of hi / lo).
 size_t lsplit_bytes(int n_max, int precision);

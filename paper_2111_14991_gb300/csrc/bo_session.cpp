@@ -505,10 +505,11 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   v.var = var;
   std::vector<double> t64((size_t)D.d * 256, 0.0);
   std::vector<float> t32((size_t)D.d * 256, 0.0f);
+  const double cs = coord_scale(D.nu, D.lengthscale);
   for (int p = 0; p < D.d; ++p)
     for (int i = 0; i < D.n_values[p]; ++i) {
       t64[(size_t)p * 256 + i] = D.values[p][i];
-      t32[(size_t)p * 256 + i] = (float)D.values[p][i];
+      t32[(size_t)p * 256 + i] = (float)(D.values[p][i] * cs);
     }
   cudaError_t e = cudaMemcpyAsync(dcodes, codes.data(), codes.size(), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(vt64, t64.data(), t64.size() * 8, cudaMemcpyHostToDevice, s->stream);

@@ -63,7 +63,7 @@ __global__ void obs_k_kernel(DevView v, int n, long long idx, double y_raw) {
   if (blockIdx.x == 0 && threadIdx.x < v.d) {
     const double x = coord64(v, idx, threadIdx.x);
     v.X[(size_t)n * v.d + threadIdx.x] = x;
-    v.Xf[(size_t)n * v.d + threadIdx.x] = (float)x;
+    v.Xf[(size_t)n * v.d + threadIdx.x] = (float)(x * (1.4426950408889634 * c));
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     v.y[n] = y_raw;
@@ -91,20 +91,41 @@ __global__ void obs_l_kernel(DevView v, int n) {
   if (warp >= n) return;
   const double* row = v.linv + (size_t)warp * v.n_max;
   double s = 0.0;
+#pragma unroll 4
   for (int j = lane; j <= warp; j += 32) s = fma(row[j], v.kvec[j], s);
   s = warp_sum(s);
   if (lane == 0) v.lvec[warp] = s;
 }
 
 // --- K3c: partial w = L^-T l over row segments of 64 ---------------------------
+// Block (column block of 32, row segment of 64): lane = column, warp w sums
+// rows seg*64 + 8w .. +8 with all eight loads in flight; L^-1[i][j] = 0 for j > i.
 __global__ void obs_w_kernel(DevView v, int n) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int seg = blockIdx.y;
-  if (j >= n) return;
-  const int i0 = max(j, seg * 64), i1 = min(n, seg * 64 + 64);
+  __shared__ double part[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  const int i0 = blockIdx.y * 64 + w * 8;
   double s = 0.0;
-  for (int i = i0; i < i1; ++i) s = fma(v.linv[(size_t)i * v.n_max + j], v.lvec[i], s);
-  v.wvec[(size_t)seg * v.n_max + j] = s;
+  if (j < n) {
+    double a[8], b[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = i0 + r;
+      const bool in = i < n && i >= j;
+      a[r] = in ? v.linv[(size_t)i * v.n_max + j] : 0.0;
+      b[r] = in ? v.lvec[i] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) s = fma(a[r], b[r], s);
+  }
+  part[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && j < n) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += part[q][lane];
+    v.wvec[(size_t)blockIdx.y * v.n_max + j] = t;
+  }
 }
 
 // --- K3d: pivot, new row n of L^-1 and its split copy (one block) --------------
@@ -135,7 +156,9 @@ __global__ void obs_finish_kernel(DevView v, int n) {
     double val;
     if (j < n) {
       double w = 0.0;
-      for (int s = 0; s < nseg; ++s) w += v.wvec[(size_t)s * v.n_max + j];
+#pragma unroll
+      for (int s = 0; s < 8; ++s)
+        if (s < nseg) w += v.wvec[(size_t)s * v.n_max + j];
       val = -w * dinv;
     } else {
       val = dinv;
@@ -209,15 +232,15 @@ int launch_observe_update(const DevView& v, int n, int64_t idx, double y_raw, do
                           double y_std, cudaStream_t s) {
   // n = observations fitted before this one; the new one becomes row n.
   int launches = 0;
-  obs_k_kernel<<<(n + 127) / 128 + (n == 0), 128, 0, s>>>(v, n, (long long)idx, y_raw);
+  obs_k_kernel<<<(n + 31) / 32 + (n == 0), 32, 0, s>>>(v, n, (long long)idx, y_raw);
   ++launches;
   if (n > 0) {
     obs_l_kernel<<<(n + 7) / 8, 256, 0, s>>>(v, n);
-    dim3 gw((n + 127) / 128, (n + 63) / 64);
-    obs_w_kernel<<<gw, 128, 0, s>>>(v, n);
+    dim3 gw((n + 31) / 32, (n + 63) / 64);
+    obs_w_kernel<<<gw, 256, 0, s>>>(v, n);
     launches += 2;
   }
-  obs_finish_kernel<<<1, 256, 0, s>>>(v, n);
+  obs_finish_kernel<<<1, 512, 0, s>>>(v, n);
   const int rows = n + 1;
   obs_beta_kernel<<<(rows + 7) / 8, 256, 0, s>>>(v, rows, y_mean, 1.0 / y_std);
   launches += 2;

@@ -280,7 +280,9 @@ def clustered_observations(land: Landscape, count: int, seed: int, n_random: int
     region the way acquisition-driven picks do."""
     n_valid = land.space.n_valid
     rng = np.random.default_rng(seed + 5000)
-    first = random_initial_sample(n_valid, n_random, seed)
+    first = random_initial_sample(n_valid, min(n_random, count), seed)
+    if count <= len(first):
+        return first[:count]
     cand = np.arange(n_valid) if n_valid <= pool else rng.choice(n_valid, pool, replace=False)
     cand = np.setdiff1d(cand, first)
     t = land.clean(cand)
