@@ -188,6 +188,54 @@ int bo_replay_enqueue(bo_space* space, const int64_t* idx_host, const double* y_
 /* Synchronize and copy the results of the last bo_replay_enqueue. */
 int bo_replay_fetch(bo_space* space, bo_pass_result* results_host, int32_t steps);
 
+/* ---- acquisition without any allocation -------------------------------- */
+/* No counterpart in the paper.  Some callers cannot allocate device memory
+ * where they need a suggestion: code running inside a memory pool or arena
+ * that must not grow, a process whose device memory is reserved up front by
+ * another framework, or a real-time loop where an allocation (and the
+ * synchronization it may bring) is not allowed.  For them this entry point
+ * runs the acquisition and masked top-k (the same kernel bo_suggest uses) on
+ * posterior arrays the caller already owns, and allocates nothing: its
+ * per-block scratch is one fixed array of 147,520 bytes inside this library,
+ * present on every device that loads it until the process exits.
+ *
+ * mu, var     device arrays [n_cand] of float (f64 = 0) or double (f64 = 1):
+ *             posterior mean and variance, standardized units
+ * visited     device array [ceil(n_cand / 32)] of uint32, bit i = candidate i
+ *             evaluated (skipped)
+ * params      host struct below, read before return
+ * result      device bo_pass_result written by the kernel (status, lambda,
+ *             mean variance, top-3 per acquisition function)
+ * stream      cudaStream_t (NULL = legacy default stream)
+ *
+ * Returns BO_ERR_CAPACITY for n_cand > BO_NOALLOC_MAX_CAND (the scratch holds
+ * the partial results of at most 1,024 blocks of 4,096 candidates),
+ * BO_ERR_ARG for bad arguments, BO_ERR_CUDA if a launch fails.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, no allocation) with that device current; make that
+ * first call before any stream capture.  Every call shares the one array and
+ * its last-block counter, which each call resets to zero first: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race. */
+#define BO_NOALLOC_MAX_CAND 4194304
+
+typedef struct bo_acq_params {
+  int64_t n_cand;         /* candidates in mu / var / visited                     */
+  int64_t n_unvisited;    /* valid, non-evaluated candidates (mean-variance count) */
+  double sum_var;         /* sum of their variances                               */
+  int32_t n_af;           /* active acquisition functions, 1..3                   */
+  int32_t af[3];          /* BO_AF_EI / BO_AF_PI / BO_AF_LCB                      */
+  int32_t explore;        /* BO_EXPLORE_CV or BO_EXPLORE_CONST                    */
+  int32_t n_fit;          /* copied into the result                               */
+  double lambda_const;    /* exploration factor when explore == CONST             */
+  double fplus;           /* best observation, standardized units                 */
+  double fplus_raw;       /* best observation, raw units (> 0 for CV)             */
+  double mu_s_raw;        /* mean of the initial sample, raw units (> 0 for CV)    */
+  double mean_var_s;      /* contextual-variance baseline; <= 0: this pass's mean */
+} bo_acq_params;
+
+int bo_acquire_noalloc(const void* mu, const void* var, const uint32_t* visited, int32_t f64,
+                       const bo_acq_params* params, bo_pass_result* result, void* stream);
+
 /* Number of kernel launches this library has issued on the space so far. */
 int bo_launch_count(const bo_space* space, int64_t* out);
 

@@ -58,6 +58,13 @@ class PassResult(C.Structure):
                 ("top_sigma", (C.c_double * 3) * 3)]
 
 
+class AcqParams(C.Structure):
+    _fields_ = [("n_cand", C.c_int64), ("n_unvisited", C.c_int64), ("sum_var", C.c_double),
+                ("n_af", C.c_int32), ("af", C.c_int32 * 3), ("explore", C.c_int32),
+                ("n_fit", C.c_int32), ("lambda_const", C.c_double), ("fplus", C.c_double),
+                ("fplus_raw", C.c_double), ("mu_s_raw", C.c_double), ("mean_var_s", C.c_double)]
+
+
 # every symbol include/bo_suggest.h declares, with (restype, argtypes)
 SIGNATURES = {
     "bo_space_desc_init": (None, [C.POINTER(SpaceDesc)]),
@@ -74,6 +81,8 @@ SIGNATURES = {
     "bo_replay_enqueue": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "bo_replay_fetch": (C.c_int, [C.c_void_p, C.POINTER(PassResult), C.c_int32]),
     "bo_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "bo_acquire_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                     C.POINTER(AcqParams), C.c_void_p, C.c_void_p]),
     "bo_last_error": (C.c_char_p, []),
 }
 
@@ -242,6 +251,13 @@ class Space:
         n = C.c_int64()
         _check(lib().bo_launch_count(self._h, C.byref(n)))
         return n.value
+
+
+def acquire_noalloc(mu_ptr, var_ptr, visited_ptr, f64, params, result_ptr, stream_ptr):
+    """bo_acquire_noalloc on caller-owned device pointers (see include/bo_suggest.h)."""
+    _check(lib().bo_acquire_noalloc(C.c_void_p(mu_ptr), C.c_void_p(var_ptr), C.c_void_p(visited_ptr),
+                                    int(f64), C.byref(params), C.c_void_p(result_ptr),
+                                    C.c_void_p(stream_ptr)))
 
 
 def pass_result_dict(r):

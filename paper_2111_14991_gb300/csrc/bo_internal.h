@@ -119,6 +119,9 @@ inline double coord_scale(double nu, double lengthscale) {
   return 1.4426950408889634 * __builtin_sqrt(2.0 * nu) / lengthscale;
 }
 
+// Record an error for bo_last_error() on this thread; returns code.
+int report_error(int code, const char* msg);
+
 // Size in bytes of the reduced-precision chunked L^-1 copy (one of hi / lo).
 size_t lsplit_bytes(int n_max, int precision);
 

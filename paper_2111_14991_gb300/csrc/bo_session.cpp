@@ -184,6 +184,11 @@ struct Selector {
 
 }  // namespace
 
+int bo::report_error(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
+
 struct bo_space {
   bo_space_desc desc;
   int device = 0;
