@@ -122,6 +122,48 @@ def flops_per_candidate(n, d):
     return n * (n + 1) + 4 * n + n * (3 * d + 12)
 
 
+def aggregate(units, seconds, world, device="cpu"):
+    """Whole-job throughput of independent replicas: the units every rank
+    processed over the slowest rank's time (max over ranks)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(units), float(seconds)], dtype=torch.float64, device=device)
+        tot = t[:1].clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        mx = t[1:].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        units, seconds = float(tot.item()), float(mx.item())
+    return units / seconds, seconds
+
+
+def kernel_only(args):
+    """Build the final-state session and launch the prediction kernel a few
+    times (the command the ncu captures profile)."""
+    import torch
+    from paper_2111_14991_gb300 import Space, build
+    build.build()
+    cfg = CONFIGS[args.config]
+    sp = space_for(args.config)
+    idx, y = observations(sp, args.config, cfg["n_final"], seed=0)
+    s = Space(sp.grids, sp.invalid, precision=args.precision, n_max=max(cfg["n_final"], 32))
+    for i, v in zip(idx, y):
+        s.observe(int(i), float(v))
+    s.sync()
+    st = torch.cuda.current_stream()
+    ts = []
+    for _ in range(args.kernel_only):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.predict_enqueue()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    s.close()
+    print(json.dumps({"kernel_only": args.kernel_only, "config": cfg["name"], "precision": args.precision,
+                      "n": cfg["n_final"], "ms": ts}))
+
+
 def tc_mma_flops(n, N):
     """Tensor-core flops the FP16X3 / BF16X3 kernel issues: 3 products, 32-wide
     chunks, each chunk's N range running from its first row to n_pad."""
@@ -267,13 +309,8 @@ def run_ours(args, rank, world):
                 "n_obs": f"{f['n0'] + 4}..{f['n_last']}",
                 "roofline": roofline_for(fprec, f["n_last"], f["sp"].d, f["sp"].n_valid, f["k1"])}
 
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([tot, e2e_tot], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot, e2e_tot = tt.tolist()
-    value = m["scored"] * world / tot
-    e2e_value = e2e_scored * world / e2e_tot
+    value, tot = aggregate(m["scored"], tot, world, "cuda")
+    e2e_value, e2e_tot = aggregate(e2e_scored, e2e_tot, world, "cuda")
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "candidates/s", "n_gpus": world,
         "steps": steps, "warmup": warm, "ms_per_step": round(1e3 * tot / steps, 4),
@@ -377,6 +414,8 @@ def main():
     ap.add_argument("--latency-reps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
+    ap.add_argument("--kernel-only", type=int, default=0,
+                    help="only launch the prediction kernel this many times at the final state")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", 0))
@@ -384,6 +423,9 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args)
+        return
+    if args.kernel_only:
+        kernel_only(args)
         return
     if world > 1:
         import torch

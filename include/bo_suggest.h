@@ -149,6 +149,11 @@ int bo_suggest(bo_space* space, int64_t* idx_out, bo_suggest_info* info);
  * var clamped at 0).  Synchronous.  For inspection and tests. */
 int bo_predict(bo_space* space, int64_t begin, int64_t count, double* mu_out, double* var_out);
 
+/* Host copy of the posterior the most recent prediction pass of this space
+ * left on the device (bo_suggest, bo_predict, bo_batch_suggest, replay):
+ * valid-list indices [begin, begin + count), no recomputation.  Synchronous. */
+int bo_last_posterior(bo_space* space, int64_t begin, int64_t count, double* mu_out, double* var_out);
+
 /* Enqueue the prediction kernels for the current observations on the
  * space's stream without waiting: the posterior of every candidate lands in
  * library-owned device memory.  For overlapping and for timing the
@@ -187,6 +192,26 @@ int bo_replay_enqueue(bo_space* space, const int64_t* idx_host, const double* y_
                       int32_t steps);
 /* Synchronize and copy the results of the last bo_replay_enqueue. */
 int bo_replay_fetch(bo_space* space, bo_pass_result* results_host, int32_t steps);
+
+/* ---- batches of spaces --------------------------------------------------- */
+/* Many sessions served together (paper Sec. III-G's suggest step, batched):
+ * bo_batch_observe updates every space's surrogate in five kernel launches,
+ * bo_batch_suggest runs the prediction passes of all spaces that need one in
+ * a single persistent tensor-core launch (tiles of all spaces balanced over
+ * the SMs) and one acquisition launch, replayed from a captured CUDA graph
+ * once a batch shape repeats.  Per space the results equal bo_observe /
+ * bo_suggest.  The spaces must share device, stream, precision and nu, and
+ * stay alive while the batch exists; FP64 spaces are served one pass at a
+ * time.  status_out[i] (optional) receives each space's BO_* code; the
+ * return value is the first error or BO_OK. */
+typedef struct bo_batch bo_batch;
+int bo_batch_create(bo_space* const* spaces, int32_t count, bo_batch** out);
+int bo_batch_destroy(bo_batch* batch);
+/* idx[i] < 0 leaves space i unchanged; asynchronous on the spaces' stream. */
+int bo_batch_observe(bo_batch* batch, const int64_t* idx, const double* values, int32_t* status_out);
+/* idx_out[count]; info_out (optional) [count]. Synchronous. */
+int bo_batch_suggest(bo_batch* batch, int64_t* idx_out, int32_t* status_out, bo_suggest_info* info_out);
+int bo_batch_launch_count(const bo_batch* batch, int64_t* out);
 
 /* ---- acquisition without any allocation -------------------------------- */
 /* No counterpart in the paper.  Some callers cannot allocate device memory

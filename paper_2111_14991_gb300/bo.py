@@ -76,6 +76,12 @@ SIGNATURES = {
     "bo_suggest": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(SuggestInfo)]),
     "bo_predict": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]),
     "bo_predict_enqueue": (C.c_int, [C.c_void_p]),
+    "bo_last_posterior": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]),
+    "bo_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    "bo_batch_destroy": (C.c_int, [C.c_void_p]),
+    "bo_batch_observe": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "bo_batch_suggest": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SuggestInfo)]),
+    "bo_batch_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "bo_get_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "bo_sync": (C.c_int, [C.c_void_p]),
     "bo_replay_enqueue": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
@@ -210,15 +216,20 @@ class Space:
         idx = C.c_int64()
         info = SuggestInfo()
         _check(lib().bo_suggest(self._h, C.byref(idx), C.byref(info)))
-        return dict(idx=idx.value, af=AF_NAMES.get(info.af), predicted=bool(info.predicted),
-                    mu=info.mu, sigma=info.sigma, score=info.score, lam=info.lam,
-                    mean_var=info.mean_var, n_scored=info.n_scored)
+        return _info_dict(info)
 
     def predict(self, begin=0, count=None):
         count = self.N - begin if count is None else count
         mu = np.empty(count, dtype=np.float64)
         var = np.empty(count, dtype=np.float64)
         _check(lib().bo_predict(self._h, begin, count, mu.ctypes.data, var.ctypes.data))
+        return mu, var
+
+    def last_posterior(self, begin=0, count=None):
+        count = self.N - begin if count is None else count
+        mu = np.empty(count, dtype=np.float64)
+        var = np.empty(count, dtype=np.float64)
+        _check(lib().bo_last_posterior(self._h, begin, count, mu.ctypes.data, var.ctypes.data))
         return mu, var
 
     def predict_enqueue(self):
@@ -251,6 +262,58 @@ class Space:
         n = C.c_int64()
         _check(lib().bo_launch_count(self._h, C.byref(n)))
         return n.value
+
+
+def _info_dict(info):
+    return dict(idx=info.idx, af=AF_NAMES.get(info.af), predicted=bool(info.predicted), mu=info.mu,
+                sigma=info.sigma, score=info.score, lam=info.lam, mean_var=info.mean_var,
+                n_scored=info.n_scored)
+
+
+class Batch:
+    """Spaces observed and suggested together (one launch per phase for all)."""
+
+    def __init__(self, spaces):
+        self.spaces = list(spaces)
+        arr = (C.c_void_p * len(self.spaces))(*[s._h for s in self.spaces])
+        h = C.c_void_p()
+        _check(lib().bo_batch_create(arr, len(self.spaces), C.byref(h)))
+        self._h = h
+
+    def observe(self, idx, values):
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        values = np.ascontiguousarray(values, dtype=np.float64)
+        status = np.zeros(len(self.spaces), dtype=np.int32)
+        rc = lib().bo_batch_observe(self._h, idx.ctypes.data, values.ctypes.data, status.ctypes.data)
+        if rc != BO_OK and not status.any():
+            _check(rc)
+        return status
+
+    def suggest(self):
+        n = len(self.spaces)
+        idx = np.zeros(n, dtype=np.int64)
+        status = np.zeros(n, dtype=np.int32)
+        infos = (SuggestInfo * n)()
+        rc = lib().bo_batch_suggest(self._h, idx.ctypes.data, status.ctypes.data, infos)
+        if rc != BO_OK and not status.any():
+            _check(rc)
+        return idx, status, [_info_dict(i) for i in infos]
+
+    def launch_count(self):
+        n = C.c_int64()
+        _check(lib().bo_batch_launch_count(self._h, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().bo_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def acquire_noalloc(mu_ptr, var_ptr, visited_ptr, f64, params, result_ptr, stream_ptr):

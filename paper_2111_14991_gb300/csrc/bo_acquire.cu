@@ -111,8 +111,11 @@ __device__ __forceinline__ T score(int af, T mu, T sigma, T fplus, T lam) {
   return delta * Phi + sigma * phi;
 }
 
+// One block's share of the acquisition pass over v: blocks [0, nblocks) of
+// the pass stride over the candidates; the last one to finish merges.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a) {
+__device__ __forceinline__ void acquire_body(const AcqDev& v, const PassArgs& a, const int block, const int nblocks,
+                                             const double sum_var) {
   static_assert(kMaxK == 3, "top_insert is written for three entries");
   __shared__ Top<T> s_top[kThreads / 32][3];
   __shared__ bool s_last;
@@ -120,7 +123,6 @@ __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a)
   const T* var = static_cast<const T*>(v.var);
 
   // lambda from the pass's mean variance (every block computes the same value)
-  const double sum_var = *v.sum_var;
   const double mean_var = a.n_unvisited > 0 ? sum_var / (double)a.n_unvisited : 0.0;
   const double var_s = a.first_pass ? mean_var : *v.var_s;
   double lam = a.lambda_const;
@@ -131,8 +133,8 @@ __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a)
   Top<T> top[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) top_init(top[q]);
-  const int64_t stride = (int64_t)gridDim.x * kThreads;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < v.N; i += stride) {
+  const int64_t stride = (int64_t)nblocks * kThreads;
+  for (int64_t i = (int64_t)block * kThreads + threadIdx.x; i < v.N; i += stride) {
     if ((v.visited[i >> 5] >> (i & 31)) & 1u) continue;
     const T m = mu[i];
     const T vv = var[i];
@@ -156,14 +158,14 @@ __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a)
     const int q = threadIdx.x;
     Top<T> t = s_top[0][q];
     for (int w = 1; w < kThreads / 32; ++w) top_merge(t, s_top[w][q]);
-    TopEntry* out = v.partial + ((size_t)blockIdx.x * 3 + q) * kMaxK;
+    TopEntry* out = v.partial + ((size_t)block * 3 + q) * kMaxK;
     for (int r = 0; r < kMaxK; ++r) { out[r].score = (double)t.s[r]; out[r].idx = t.i[r]; }
     __threadfence();
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int done = atomicAdd(v.counter, 1u);
-    s_last = (done == gridDim.x - 1);
+    s_last = (done == (unsigned)nblocks - 1);
   }
   __syncthreads();
   if (!s_last) return;
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a)
   Top<T> fin[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) top_init(fin[q]);
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += kThreads)
+  for (int b = threadIdx.x; b < nblocks; b += kThreads)
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const volatile TopEntry* in = v.partial + ((size_t)b * 3 + q) * kMaxK;
@@ -216,6 +218,24 @@ __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a)
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a) {
+  acquire_body<T>(v, a, blockIdx.x, gridDim.x, *v.sum_var);
+}
+
+// Many spaces in one launch: block b serves item block_item[b] as its
+// block_local[b]-th block; the item's variance sum is the sum, in segment
+// order, of the epilogue parts of its tensor-core segments.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) acquire_batch_kernel(const AcqItem* items, const int* block_item,
+                                                                 const int* block_local, const double* seg_part) {
+  const AcqItem& it = items[block_item[blockIdx.x]];
+  double sum_var = 0.0;
+  for (int g = it.seg0; g < it.seg1; ++g)
+    for (int e = 0; e < 4; ++e) sum_var += seg_part[(size_t)g * 4 + e];
+  acquire_body<T>(it.dev, it.args, block_local[blockIdx.x], it.nblocks, sum_var);
+}
+
 }  // namespace
 
 int acquire_grid(int64_t n_cand, int max_blocks) {
@@ -229,6 +249,15 @@ int launch_acquire(const AcqDev& v, const PassArgs& a, bool f64, cudaStream_t s)
     acquire_kernel<double><<<grid, kThreads, 0, s>>>(v, a);
   else
     acquire_kernel<float><<<grid, kThreads, 0, s>>>(v, a);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_acquire_batch(const AcqItem* items, const int* block_item, const int* block_local,
+                         const double* seg_part, int total_blocks, bool f64, cudaStream_t s) {
+  if (f64)
+    acquire_batch_kernel<double><<<total_blocks, kThreads, 0, s>>>(items, block_item, block_local, seg_part);
+  else
+    acquire_batch_kernel<float><<<total_blocks, kThreads, 0, s>>>(items, block_item, block_local, seg_part);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 

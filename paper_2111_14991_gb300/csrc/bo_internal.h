@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -48,7 +49,8 @@ struct DevView {
   uint32_t* visited;         // [ceil(N/32)] bit i = configuration i evaluated
 
   double* X;                 // [n_max][d] coordinates of fitted observations
-  float* Xf;                 // [n_max][d] FP32 copy, scaled as vtab32
+  float* Xf;                 // [16][n_max] FP32 copy, transposed and scaled as vtab32;
+                             // rows >= d and columns >= n stay zero
   double* y;                 // [n_max] raw fitted values
   double* linv;              // [n_max][n_max] L^-1, row-major, lower triangular
   double* beta;              // [n_max] L^-1 y~
@@ -72,6 +74,9 @@ struct DevView {
   bo_pass_result* results;   // [max_results]
   int max_results;
 };
+
+// Maximum coordinate rows of the transposed FP32 observation copy.
+constexpr int kXfRows = 16;
 
 // Scalars of one prediction pass known to the host.
 struct PassArgs {
@@ -103,15 +108,83 @@ struct AcqDev {
   bo_pass_result* result;
 };
 
+// One space as the tensor-core pass sees it (device pointers and sizes).
+struct TcSess {
+  const uint8_t* codes;      // [d][N_pad]
+  const float* vtab32;       // [d][256] scaled values
+  const uint32_t* visited;
+  const float* xf;           // [kXfRows][n_max] scaled observation coordinates
+  const float* rowq;
+  const float* rowb;
+  const uint8_t* lhi;        // chunked split copy of L^-1
+  const uint8_t* llo;
+  float* mu;
+  float* var;
+  int64_t N, N_pad;
+  int d, n, n_pad, n_max, chunks, num_tiles;
+};
+
+// Tiles [tile0, tile1) of space sess, processed in order by one CTA.
+struct TcSeg {
+  int sess, tile0, tile1;
+};
+
+// A batched tensor-core launch: device arrays the host planned and uploaded.
+struct TcBatchLaunch {
+  const TcSess* sess;        // [count]
+  const TcSeg* segs;         // [num_segs]
+  const int* seg_begin;      // [grid + 1]
+  double* seg_part;          // [num_segs][4] variance sums written by the kernel
+  int32_t* status;           // BO_ERR_TIMEOUT lands here
+  int count, grid, precision, dmax, n_pad_max;
+  double nu;
+};
+
+// One space of a batched acquisition launch.
+struct AcqItem {
+  AcqDev dev;                // dev.sum_var unused: the sum comes from seg_part[seg0, seg1)
+  PassArgs args;
+  int nblocks;               // blocks serving this space
+  int seg0, seg1;            // its tensor-core segments
+};
+
+// One observation update of a batch (the arguments of the single-space launch).
+struct ObsItem {
+  DevView v;
+  int n;                     // observations fitted before this one
+  long long idx;
+  double y_raw, y_mean, inv_std;
+};
+struct ObsBlock {
+  int item, local;           // space and its block index within one phase
+};
+struct VisitItem {
+  uint32_t* visited;         // a non-finite observation only sets its evaluated bit
+  long long idx;
+};
+
 // ---- launchers (each returns the number of kernels it launched, or -1) ----
 int launch_observe_update(const DevView& v, int n, int64_t idx, double y_raw, double y_mean,
                           double y_std, cudaStream_t s);
 int launch_set_visited(const DevView& v, int64_t idx, cudaStream_t s);
+// Block tables of the batched update phases k, l, w, beta (concatenated) for spaces with
+// n[i] observations fitted before their new one; counts[] receives each phase's block count.
+void obs_batch_blocks(const int* n, int count, std::vector<ObsBlock>* blocks, int counts[4]);
+int launch_observe_batch(const ObsItem* items, int count, const ObsBlock* blocks, const int counts[4],
+                         const VisitItem* visits, int n_visits, cudaStream_t s);
 int launch_predict_f64(const DevView& v, int n, int64_t n_unvisited, cudaStream_t s);
 int launch_predict_tc(const DevView& v, int n, int64_t n_unvisited, cudaStream_t s);
+TcSess tc_session(const DevView& v, int n);
+int tc_dim_bucket(int d);
+// Cost-balanced segments of `count` spaces over `grid` CTAs; returns the segment count.
+int tc_plan_batch(const TcSess* sess, int count, int dmax, int grid, std::vector<TcSeg>* segs,
+                  std::vector<int>* seg_begin);
+int launch_predict_tc_batch(const TcBatchLaunch& L, cudaStream_t s);
 int launch_acquire(const DevView& v, const PassArgs& a, cudaStream_t s);
 int launch_acquire(const AcqDev& v, const PassArgs& a, bool f64, cudaStream_t s);
 int acquire_grid(int64_t n_cand, int max_blocks);
+int launch_acquire_batch(const AcqItem* items, const int* block_item, const int* block_local,
+                         const double* seg_part, int total_blocks, bool f64, cudaStream_t s);
 
 // Scale of the FP32 coordinate copies: distances in these units are
 // u = sqrt(2 nu) r / l * log2(e), so e^-t = 2^-u with t = sqrt(2 nu) r / l.

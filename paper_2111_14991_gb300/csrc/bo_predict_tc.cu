@@ -10,6 +10,11 @@
 // The FP64 L^-1, beta and the update stay in FP64 (bo_update.cu), which
 // writes the split copy of each new row once.
 //
+// One kernel serves one space (tiles strided over the CTAs) or a batch of
+// spaces of different sizes in one persistent launch (each CTA walks a
+// host-planned list of segments, i.e. runs of consecutive tiles of one
+// space, balanced by estimated tile cost).
+//
 // CTA organisation (persistent, one CTA per SM, 128 candidates per tile):
 //   warps 0-15   produce K* chunks: thread (row = t % 128, quarter = t / 128)
 //                evaluates the Matern covariance of its candidate against a
@@ -20,9 +25,11 @@
 //                is double-buffered, so a tile's MMAs overlap the previous
 //                tile's drain.
 //   warp 20      issues the MMAs (one thread) and owns the TMEM allocation.
-//   warp 21      streams the L^-1 chunks with bulk copies (one thread), in
-//                pieces of at most 256 rows: a 4-slot ring, or all pieces of a
-//                tile kept resident when they fit (n <= ~256), loaded once.
+//   warp 21      streams, with bulk copies (one thread), each space's
+//                observation coordinates into shared memory (double-buffered
+//                across spaces) and the L^-1 chunks in pieces of at most 256
+//                rows: a 4-slot ring, or, for one space whose pieces fit, all
+//                pieces resident, loaded once.
 // K chunk c covers observations j in [c CW, (c+1) CW); only output columns
 // k >= c CW receive it (L^-1 is lower triangular), so the MMA N range
 // shrinks along the chunks.  Every wait is bounded in time: on expiry the
@@ -31,6 +38,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "bo_internal.h"
 
@@ -50,16 +58,65 @@ constexpr int kPieceRows = 256;         // rows of L^-1 per B piece (= max MMA N
 constexpr int kMaxBSlots = 16;
 
 struct TcParams {
-  DevView v;
-  int n, n_pad, chunks, cw, parts, stages_a;
+  TcSess s0;                 // the space, when batch == 0
+  const TcSess* sess;        // batch > 0: [batch] device array
+  const TcSeg* segs;         // batch > 0: segments; CTA b owns [seg_begin[b], seg_begin[b+1])
+  const int* seg_begin;
+  double* seg_part;          // batch > 0: [segment][4] variance sums of the epilogue warps
+  double* partial;           // batch == 0: per-CTA variance sums
+  DevStats* stats;           // batch == 0: last-block total; status word of the launch
+  int32_t* status;
+  int batch;
+  int cw, parts, stages_a;
   int tmem_cols;             // columns of one accumulator buffer
   int acc_stages;            // 1 or 2 accumulator buffers
-  int num_tiles;
+  int xs_bufs;               // 1 or 2 coordinate buffers
   // B (the split L^-1 chunks) in pieces of <= 256 rows: either a ring of
-  // b_slots fixed-size slots, or every piece of a tile resident (loaded once)
+  // b_slots fixed-size slots, or every piece of the space resident (loaded once)
   int b_resident, b_slots;
-  size_t off_b, b_slot_bytes, off_x, off_q, off_bar;
+  size_t off_b, b_slot_bytes, off_x, x_buf_bytes, off_bar;
 };
+
+// Position in a CTA's work: one space with strided tiles, or a segment list.
+struct Work {
+  int seg, seg_end, sess, tile, tile_end;
+};
+
+__device__ __forceinline__ bool work_begin(const TcParams& P, Work& w) {
+  if (P.batch == 0) {
+    w.sess = 0;
+    w.tile = blockIdx.x;
+    w.tile_end = P.s0.num_tiles;
+    w.seg = w.seg_end = 0;
+    return w.tile < w.tile_end;
+  }
+  w.seg = P.seg_begin[blockIdx.x];
+  w.seg_end = P.seg_begin[blockIdx.x + 1];
+  if (w.seg >= w.seg_end) return false;
+  const TcSeg g = P.segs[w.seg];
+  w.sess = g.sess;
+  w.tile = g.tile0;
+  w.tile_end = g.tile1;
+  return w.tile < w.tile_end;
+}
+
+__device__ __forceinline__ bool work_next(const TcParams& P, Work& w) {
+  if (P.batch == 0) {
+    w.tile += gridDim.x;
+    return w.tile < w.tile_end;
+  }
+  if (++w.tile < w.tile_end) return true;
+  if (++w.seg >= w.seg_end) return false;
+  const TcSeg g = P.segs[w.seg];
+  w.sess = g.sess;
+  w.tile = g.tile0;
+  w.tile_end = g.tile1;
+  return w.tile < w.tile_end;
+}
+
+__device__ __forceinline__ const TcSess& sess_of(const TcParams& P, int s) {
+  return P.batch == 0 ? P.s0 : P.sess[s];
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -268,34 +325,36 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 template <int MODE, int DMAX, bool NU52>
 __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_constant__ TcParams P) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  const DevView& v = P.v;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int d = v.d;
-  const int n_pad = P.n_pad, chunks = P.chunks, cw = P.cw, parts = P.parts, SA = P.stages_a;
+  const int cw = P.cw, parts = P.parts, SA = P.stages_a, XB = P.xs_bufs;
   uint8_t* sa = smem;                                   // [SA][parts][8 KB]
   uint8_t* sb = smem + P.off_b;                         // B slots or resident pieces
-  float* Xs = reinterpret_cast<float*>(smem + P.off_x); // [DMAX][n_pad], rows >= d zero
-  float* Qs = reinterpret_cast<float*>(smem + P.off_q); // [n_pad] 1/s_k^2
-  float* Bs = Qs + n_pad;                               // [n_pad] beta_k/s_k
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P.off_bar);
   uint64_t* a_full = bars;
   uint64_t* a_empty = bars + SA;
-  uint64_t* b_full = bars + 2 * SA;                  // [kMaxBSlots]
-  uint64_t* b_empty = bars + 2 * SA + kMaxBSlots;    // [kMaxBSlots]
-  uint64_t* acc_full = bars + 2 * SA + 2 * kMaxBSlots;       // [2]
-  uint64_t* acc_empty = bars + 2 * SA + 2 * kMaxBSlots + 2;  // [2]
-  uint64_t* drain = bars + 2 * SA + 2 * kMaxBSlots + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SA + 2 * kMaxBSlots + 5);
+  uint64_t* b_full = bars + 2 * SA;                            // [kMaxBSlots]
+  uint64_t* b_empty = bars + 2 * SA + kMaxBSlots;              // [kMaxBSlots]
+  uint64_t* acc_full = bars + 2 * SA + 2 * kMaxBSlots;         // [2]
+  uint64_t* acc_empty = bars + 2 * SA + 2 * kMaxBSlots + 2;    // [2]
+  uint64_t* xs_full = bars + 2 * SA + 2 * kMaxBSlots + 4;      // [2]
+  uint64_t* xs_empty = bars + 2 * SA + 2 * kMaxBSlots + 6;     // [2]
+  uint64_t* drain = bars + 2 * SA + 2 * kMaxBSlots + 8;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SA + 2 * kMaxBSlots + 9);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ double red[4];   // per epilogue warp
   __shared__ bool s_last;
-  int32_t* status = &v.stats->status;
+  int32_t* status = P.status;
 
-  // ---- setup: barriers, TMEM, observation coordinates, per-row factors
+  // ---- setup: barriers, TMEM
   if (threadIdx.x == 0) {
     for (int s = 0; s < SA; ++s) { mbar_init(&a_full[s], kProducerWarps); mbar_init(&a_empty[s], 1); }
     for (int s = 0; s < kMaxBSlots; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
-    for (int s = 0; s < 2; ++s) { mbar_init(&acc_full[s], 1); mbar_init(&acc_empty[s], 4); }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&acc_full[s], 1);
+      mbar_init(&acc_empty[s], 4);
+      mbar_init(&xs_full[s], 1);
+      mbar_init(&xs_empty[s], kProducerWarps);
+    }
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -305,18 +364,11 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
                  "r"(P.tmem_cols * P.acc_stages) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  for (int e = threadIdx.x; e < DMAX * n_pad; e += kThreads) {
-    const int p = e / n_pad, j = e - p * n_pad;
-    Xs[e] = (j < P.n && p < d) ? v.Xf[(size_t)j * d + p] : 0.0f;
-  }
-  for (int k = threadIdx.x; k < n_pad; k += kThreads) {
-    Qs[k] = k < P.n ? v.rowq[k] : 0.0f;
-    Bs[k] = k < P.n ? v.rowb[k] : 0.0f;
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t xs_base = smem_addr(smem + P.off_x);
   double vsum = 0.0;
 
   if (warp < kProducerWarps) {
@@ -325,17 +377,39 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     const int quarter = threadIdx.x >> 7;
     const int jq = cw / 4;                       // observations per thread per chunk: 8 or 4
     const uint32_t a_base = smem_addr(sa);
-    const uint32_t xs_base = smem_addr(Xs);
     const uint32_t row_off = (uint32_t)((row >> 3) * (kChunkBytes * 8) + (row & 7) * 16 + quarter * 128);
     bool ok = true;
-    int s = 0;
-    uint32_t ph = 0;                            // ring slot and its phase
-    for (int tile = blockIdx.x; tile < P.num_tiles && ok; tile += gridDim.x) {
-      const int64_t cand = (int64_t)tile * kRows + row;
+    int s = 0, ks = -1, prev = -1;
+    uint32_t ph = 0;                             // ring slot and its phase
+    int n_pad = 0, chunks = 0, d = 0;
+    int64_t N_pad = 0;
+    const uint8_t* codes = nullptr;
+    const float* vt = nullptr;
+    uint32_t xs = xs_base;
+    Work w;
+    for (bool more = work_begin(P, w); more && ok; more = work_next(P, w)) {
+      if (w.sess != prev) {                      // next space: its coordinates, once copied in
+        if (ks >= 0) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&xs_empty[ks % XB]);
+        }
+        ++ks;
+        prev = w.sess;
+        const TcSess& S = sess_of(P, w.sess);
+        n_pad = S.n_pad;
+        chunks = S.chunks;
+        d = S.d;
+        N_pad = S.N_pad;
+        codes = S.codes;
+        vt = S.vtab32;
+        xs = xs_base + (uint32_t)((ks % XB) * P.x_buf_bytes);
+        if (!(ok = mbar_wait(&xs_full[ks % XB], (uint32_t)((ks / XB) & 1), abort_flag, status))) break;
+      }
+      const int64_t cand = (int64_t)w.tile * kRows + row;
       uint64_t xcp[DMAX];                      // candidate coordinate, twice per word
 #pragma unroll
       for (int p = 0; p < DMAX; ++p) {
-        const float x = p < d ? v.vtab32[p * 256 + v.codes[(int64_t)p * v.N_pad + cand]] : 0.0f;
+        const float x = p < d ? vt[p * 256 + codes[(int64_t)p * N_pad + cand]] : 0.0f;
         xcp[p] = pk2(x, x);
       }
       for (int c = 0; c < chunks && ok; ++c) {
@@ -343,7 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         // K* for this thread's observations, computed before waiting for the ring slot:
         // squared distances two observations per packed instruction
         uint64_t r2p[4] = {0ull, 0ull, 0ull, 0ull};
-        const uint32_t xrow = xs_base + (uint32_t)(j0 * 4);
+        const uint32_t xrow = xs + (uint32_t)(j0 * 4);
 #pragma unroll
         for (int p = 0; p < DMAX; ++p) {
           uint64_t o0, o1;
@@ -362,12 +436,12 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         }
         float kv[8];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          if (2 * w < jq) {
+        for (int q = 0; q < 4; ++q) {
+          if (2 * q < jq) {
             float a, b;
-            upk2(r2p[w], a, b);
-            kv[2 * w] = matern_u2<NU52>(a);
-            kv[2 * w + 1] = matern_u2<NU52>(b);
+            upk2(r2p[q], a, b);
+            kv[2 * q] = matern_u2<NU52>(a);
+            kv[2 * q + 1] = matern_u2<NU52>(b);
           }
         }
         if (!(ok = mbar_wait(&a_empty[s], ph ^ 1, abort_flag, status))) break;
@@ -377,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         } else {
           uint32_t h[4], l[4];
 #pragma unroll
-          for (int w = 0; w < 4; ++w) split2<MODE>(kv[2 * w], kv[2 * w + 1], h[w], l[w]);
+          for (int q = 0; q < 4; ++q) split2<MODE>(kv[2 * q], kv[2 * q + 1], h[q], l[q]);
           st_shared_v4(stage, h[0], h[1], h[2], h[3]);
           st_shared_v4(stage + kPartBytes, l[0], l[1], l[2], l[3]);
         }
@@ -392,10 +466,38 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     const int e = warp - kEpiWarp0;
     const int row = e * 32 + lane;
     bool ok = true;
-    int it = 0;
-    for (int tile = blockIdx.x; tile < P.num_tiles && ok; tile += gridDim.x, ++it) {
+    int it = 0, prev = -1, seg = -1;
+    int n_pad = 0;
+    int64_t N = 0;
+    const float* rq = nullptr;
+    const float* rb = nullptr;
+    const uint32_t* visited = nullptr;
+    float* mu = nullptr;
+    float* var = nullptr;
+    Work w;
+    for (bool more = work_begin(P, w); more && ok; more = work_next(P, w), ++it) {
+      if (P.batch && w.seg != seg) {             // segment boundary: hand in its variance sum
+        if (seg >= 0) {
+          double t = vsum;
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (lane == 0) P.seg_part[(size_t)seg * 4 + e] = t;
+          vsum = 0.0;
+        }
+        seg = w.seg;
+      }
+      if (w.sess != prev) {
+        prev = w.sess;
+        const TcSess& S = sess_of(P, w.sess);
+        n_pad = S.n_pad;
+        N = S.N;
+        rq = S.rowq;
+        rb = S.rowb;
+        visited = S.visited;
+        mu = S.mu;
+        var = S.var;
+      }
       const int as = it % P.acc_stages;
-      if (!(ok = mbar_wait(&acc_full[as], (it / P.acc_stages) & 1, abort_flag, status))) break;
+      if (!(ok = mbar_wait(&acc_full[as], (uint32_t)((it / P.acc_stages) & 1), abort_flag, status))) break;
       tc_fence_after();
       float s2 = 0.0f, sm = 0.0f;
       const uint32_t lane_base = tmem + (uint32_t)(as * P.tmem_cols) + ((uint32_t)(e * 32) << 16);
@@ -404,8 +506,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         tmem_ld32(lane_base + (uint32_t)k0, acc);
 #pragma unroll
         for (int i = 0; i < 32; i += 4) {
-          const float4 q = *reinterpret_cast<const float4*>(&Qs[k0 + i]);
-          const float4 b = *reinterpret_cast<const float4*>(&Bs[k0 + i]);
+          const float4 q = __ldg(reinterpret_cast<const float4*>(rq + k0 + i));
+          const float4 b = __ldg(reinterpret_cast<const float4*>(rb + k0 + i));
           s2 = fmaf(acc[i] * acc[i], q.x, s2);
           s2 = fmaf(acc[i + 1] * acc[i + 1], q.y, s2);
           s2 = fmaf(acc[i + 2] * acc[i + 2], q.z, s2);
@@ -419,11 +521,17 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[as]);
-      const int64_t cand = (int64_t)tile * kRows + row;
-      const float var = fmaxf(0.0f, 1.0f - s2);
-      static_cast<float*>(v.mu)[cand] = sm;
-      static_cast<float*>(v.var)[cand] = var;
-      if (cand < v.N && !((v.visited[cand >> 5] >> (cand & 31)) & 1u)) vsum += (double)var;
+      const int64_t cand = (int64_t)w.tile * kRows + row;
+      const float vr = fmaxf(0.0f, 1.0f - s2);
+      mu[cand] = sm;
+      var[cand] = vr;
+      if (cand < N && !((visited[cand >> 5] >> (cand & 31)) & 1u)) vsum += (double)vr;
+    }
+    if (P.batch && seg >= 0 && ok) {
+      double t = vsum;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) P.seg_part[(size_t)seg * 4 + e] = t;
+      vsum = 0.0;
     }
   } else if (warp == kMmaWarp) {
     // ===================== MMA issuer =====================
@@ -431,11 +539,19 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
       const int fmt = MODE == BO_PREC_FP16X3 ? 0 : MODE == BO_PREC_BF16X3 ? 1 : 2;
       const uint32_t a_base = smem_addr(sa), b_base = smem_addr(sb);
       bool ok = true, issued = false;
-      int it = 0, sa_i = 0, tb = 0;
+      int it = 0, sa_i = 0, tb = 0, prev = -1, n_pad = 0, chunks = 0;
       uint32_t pha = 0, phb = 0;
-      for (int tile = blockIdx.x; tile < P.num_tiles && ok; tile += gridDim.x, ++it) {
+      Work w;
+      for (bool more = work_begin(P, w); more && ok; more = work_next(P, w), ++it) {
+        if (w.sess != prev) {
+          prev = w.sess;
+          const TcSess& S = sess_of(P, w.sess);
+          n_pad = S.n_pad;
+          chunks = S.chunks;
+        }
         const int as = it % P.acc_stages;
-        if (!(ok = mbar_wait(&acc_empty[as], ((it / P.acc_stages) & 1) ^ 1, abort_flag, status))) break;
+        if (!(ok = mbar_wait(&acc_empty[as], (uint32_t)(((it / P.acc_stages) & 1) ^ 1), abort_flag, status)))
+          break;
         tc_fence_after();
         const uint32_t d_base = tmem + (uint32_t)(as * P.tmem_cols);
         int q = 0;                  // piece index within the tile
@@ -446,8 +562,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           tc_fence_after();
           const uint32_t a_st = a_base + (uint32_t)(s * parts * kPartBytes);
           for (int r0 = c * cw; r0 < n_pad && ok; r0 += kPieceRows, ++q) {
-            const int w = min(kPieceRows, n_pad - r0);          // rows of this piece = MMA N
-            const uint32_t part_bytes = (uint32_t)((w >> 3) * 512);
+            const int wd = min(kPieceRows, n_pad - r0);         // rows of this piece = MMA N
+            const uint32_t part_bytes = (uint32_t)((wd >> 3) * 512);
             const int slot = P.b_resident ? q : tb;
             if (!(ok = mbar_wait(&b_full[slot], P.b_resident ? 0u : phb, abort_flag, status))) break;
             tc_fence_after();
@@ -457,11 +573,11 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
               // products (hi, lo), (lo, hi), (hi, hi): small terms first
               const int pa = parts == 2 ? (sp == 1 ? 1 : 0) : 0;
               const int pb = parts == 2 ? (sp == 0 ? 1 : 0) : 0;
-              for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t ad = smem_desc(a_st + (uint32_t)(pa * kPartBytes + ks * 256), 128, 512);
-                const uint64_t bd = smem_desc(b_st + (uint32_t)(pb * part_bytes + ks * 256), 128, 512);
-                const uint32_t acc = (c > 0 || sp > 0 || ks > 0) ? 1u : 0u;
-                mma<MODE>(d_base + (uint32_t)r0, ad, bd, instr_desc(fmt, kRows, w), acc);
+              for (int kk = 0; kk < 2; ++kk) {
+                const uint64_t ad = smem_desc(a_st + (uint32_t)(pa * kPartBytes + kk * 256), 128, 512);
+                const uint64_t bd = smem_desc(b_st + (uint32_t)(pb * part_bytes + kk * 256), 128, 512);
+                const uint32_t acc = (c > 0 || sp > 0 || kk > 0) ? 1u : 0u;
+                mma<MODE>(d_base + (uint32_t)r0, ad, bd, instr_desc(fmt, kRows, wd), acc);
               }
             }
             issued = true;
@@ -485,50 +601,78 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
       }
     }
   } else if (warp == kLoadWarp) {
-    // ===================== L^-1 chunk loader =====================
+    // ===================== coordinates and L^-1 pieces =====================
     if (lane == 0) {
       const int eb = MODE == BO_PREC_TF32 ? 4 : 2;
       const int ccw = kChunkBytes / eb;
       const uint32_t b_base = smem_addr(sb);
-      bool ok = true;
-      int issued[kMaxBSlots], last_phase[kMaxBSlots];
+      bool ok = true, b_loaded = false;
+      int issued[kMaxBSlots], last_phase[kMaxBSlots], xs_issued[2] = {0, 0}, xs_phase[2] = {0, 0};
       for (int t = 0; t < kMaxBSlots; ++t) issued[t] = last_phase[t] = 0;
-      int tb = 0;
+      int tb = 0, ks = -1, prev = -1, n_pad = 0, chunks = 0, n_max = 0;
       uint32_t phb = 0;
-      for (int tile = blockIdx.x; tile < P.num_tiles && ok; tile += gridDim.x) {
+      const uint8_t* lhi = nullptr;
+      const uint8_t* llo = nullptr;
+      Work w;
+      for (bool more = work_begin(P, w); more && ok; more = work_next(P, w)) {
+        if (w.sess != prev) {                    // next space: copy its coordinates in
+          ++ks;
+          prev = w.sess;
+          const TcSess& S = sess_of(P, w.sess);
+          n_pad = S.n_pad;
+          chunks = S.chunks;
+          n_max = S.n_max;
+          lhi = S.lhi;
+          llo = S.llo;
+          const int xb = ks % XB;
+          if (!(ok = mbar_wait(&xs_empty[xb], (uint32_t)(((ks / XB) & 1) ^ 1), abort_flag, status))) break;
+          const uint32_t row_bytes = (uint32_t)(n_pad * 4);
+          mbar_arrive_tx(&xs_full[xb], row_bytes * DMAX);
+          const uint32_t dst = xs_base + (uint32_t)(xb * P.x_buf_bytes);
+          for (int p = 0; p < DMAX; ++p) bulk_g2s(dst + (uint32_t)p * row_bytes, S.xf + (size_t)p * n_max, row_bytes, &xs_full[xb]);
+          xs_issued[xb] = 1;
+          xs_phase[xb] = (ks / XB) & 1;
+        }
+        if (P.b_resident && b_loaded) continue;  // every piece stays in shared memory
         int q = 0;
         uint32_t packed = 0;
         for (int c = 0; c < chunks && ok; ++c) {
-          const size_t goff = (size_t)kChunkBytes * ((size_t)c * v.n_max - (size_t)ccw * c * (c - 1) / 2);
+          const size_t goff = (size_t)kChunkBytes * ((size_t)c * n_max - (size_t)ccw * c * (c - 1) / 2);
           for (int r0 = c * ccw; r0 < n_pad && ok; r0 += kPieceRows, ++q) {
-            const int w = min(kPieceRows, n_pad - r0);
-            const uint32_t bytes = (uint32_t)((w >> 3) * 512);
+            const int wd = min(kPieceRows, n_pad - r0);
+            const uint32_t bytes = (uint32_t)((wd >> 3) * 512);
             const size_t src = goff + (size_t)(r0 - c * ccw) / 8 * 512;
             const int slot = P.b_resident ? q : tb;
             if (!P.b_resident && !(ok = mbar_wait(&b_empty[tb], phb ^ 1, abort_flag, status))) break;
             const uint32_t dst = b_base + (P.b_resident ? packed : (uint32_t)(tb * P.b_slot_bytes));
             mbar_arrive_tx(&b_full[slot], bytes * parts);
-            bulk_g2s(dst, v.lsplit_hi + src, bytes, &b_full[slot]);
-            if (parts == 2) bulk_g2s(dst + bytes, v.lsplit_lo + src, bytes, &b_full[slot]);
+            bulk_g2s(dst, lhi + src, bytes, &b_full[slot]);
+            if (parts == 2) bulk_g2s(dst + bytes, llo + src, bytes, &b_full[slot]);
             issued[slot] = 1;
             last_phase[slot] = P.b_resident ? 0 : (int)phb;
             packed += bytes * (uint32_t)parts;
             if (!P.b_resident && ++tb == P.b_slots) { tb = 0; phb ^= 1; }
           }
         }
-        if (P.b_resident) break;   // every piece stays in shared memory for all tiles
+        b_loaded = true;
       }
-      // copies land on their own; wait for the last one of each slot before exit
+      // copies land on their own; wait for the last one of each barrier before exit
       for (int t = 0; t < kMaxBSlots; ++t)
         if (issued[t]) {
           unsigned long long t0 = now_ns();
           while (!mbar_test(&b_full[t], (uint32_t)last_phase[t]) && now_ns() - t0 < kWaitNs) {
           }
         }
+      for (int t = 0; t < 2; ++t)
+        if (xs_issued[t]) {
+          unsigned long long t0 = now_ns();
+          while (!mbar_test(&xs_full[t], (uint32_t)xs_phase[t]) && now_ns() - t0 < kWaitNs) {
+          }
+        }
     }
   }
 
-  // ---- teardown: per-CTA variance sum, TMEM release, last-block total
+  // ---- teardown: TMEM release; one space: per-CTA variance sum, last-block total
   for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
   if (warp >= kEpiWarp0 && warp < kMmaWarp && lane == 0) red[warp - kEpiWarp0] = vsum;
   tc_fence_before();
@@ -538,19 +682,20 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(P.tmem_cols * P.acc_stages) : "memory");
   }
+  if (P.batch) return;
   if (threadIdx.x == 0) {
-    v.partial[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+    P.partial[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
     __threadfence();
-    const unsigned int done = atomicAdd(&v.stats->k1_done, 1u);
+    const unsigned int done = atomicAdd(&P.stats->k1_done, 1u);
     s_last = (done == gridDim.x - 1);
   }
   __syncthreads();
   if (s_last && threadIdx.x == 0) {
     __threadfence();
     double t = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)v.partial)[b];
-    v.stats->sum_var = t;
-    v.stats->k1_done = 0;
+    for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)P.partial)[b];
+    P.stats->sum_var = t;
+    P.stats->k1_done = 0;
   }
 }
 
@@ -571,8 +716,8 @@ int launch_mode(const TcParams& P, size_t smem, int grid, cudaStream_t s) {
 }
 
 template <int MODE, bool NU52>
-int launch_dims(const TcParams& P, size_t smem, int grid, cudaStream_t s) {
-  switch (dim_bucket(P.v.d)) {
+int launch_dims(const TcParams& P, int dmax, size_t smem, int grid, cudaStream_t s) {
+  switch (dmax) {
     case 4: return launch_mode<MODE, 4, NU52>(P, smem, grid, s);
     case 7: return launch_mode<MODE, 7, NU52>(P, smem, grid, s);
     case 9: return launch_mode<MODE, 9, NU52>(P, smem, grid, s);
@@ -580,68 +725,166 @@ int launch_dims(const TcParams& P, size_t smem, int grid, cudaStream_t s) {
   }
 }
 
-template <int MODE>
-int launch_nu(const TcParams& P, size_t smem, int grid, cudaStream_t s) {
-  return P.v.nu == 2.5 ? launch_dims<MODE, true>(P, smem, grid, s) : launch_dims<MODE, false>(P, smem, grid, s);
+int dispatch(const TcParams& P, int precision, double nu, int dmax, size_t smem, int grid, cudaStream_t s) {
+  const bool nu52 = nu == 2.5;
+  switch (precision) {
+    case BO_PREC_FP16X3:
+      return nu52 ? launch_dims<BO_PREC_FP16X3, true>(P, dmax, smem, grid, s)
+                  : launch_dims<BO_PREC_FP16X3, false>(P, dmax, smem, grid, s);
+    case BO_PREC_BF16X3:
+      return nu52 ? launch_dims<BO_PREC_BF16X3, true>(P, dmax, smem, grid, s)
+                  : launch_dims<BO_PREC_BF16X3, false>(P, dmax, smem, grid, s);
+    default:
+      return nu52 ? launch_dims<BO_PREC_TF32, true>(P, dmax, smem, grid, s)
+                  : launch_dims<BO_PREC_TF32, false>(P, dmax, smem, grid, s);
+  }
+}
+
+// Shared-memory plan and pipeline depths for a launch whose spaces have at
+// most n_pad_max padded observations and dmax coordinate rows.  resident_ok:
+// the B pieces of the (single) space may stay resident.  Returns the dynamic
+// shared-memory size, 0 if nothing fits.
+size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resident_ok) {
+  const int eb = precision == BO_PREC_TF32 ? 4 : 2;
+  P.cw = kChunkBytes / eb;
+  P.parts = precision == BO_PREC_TF32 ? 1 : 2;
+  int cols = 32;
+  while (cols < n_pad_max) cols <<= 1;
+  if (cols > 512) return 0;
+  P.tmem_cols = cols;
+  P.acc_stages = 2 * cols <= 512 ? 2 : 1;
+  const size_t a_stage = (size_t)P.parts * kPartBytes;
+  P.x_buf_bytes = ((size_t)dmax * n_pad_max * 4 + 127) / 128 * 128;
+  const size_t x_bytes = P.x_buf_bytes * P.xs_bufs;
+  const size_t limit = 226 * 1024;   // dynamic part; the kernel's static shared memory is small
+  size_t resident = 0;
+  int pieces = 0;
+  for (int c = 0; c < n_pad_max / P.cw; ++c)
+    for (int r0 = c * P.cw; r0 < n_pad_max; r0 += kPieceRows, ++pieces)
+      resident += (size_t)P.parts * (std::min(kPieceRows, n_pad_max - r0) / 8) * 512;
+  P.b_resident = (resident_ok && pieces <= kMaxBSlots && resident <= (size_t)P.parts * 64 * 1024) ? 1 : 0;
+  P.b_slots = 4;
+  P.b_slot_bytes = (size_t)P.parts * (kPieceRows / 8) * 512;
+  const size_t b_bytes = P.b_resident ? resident : P.b_slots * P.b_slot_bytes;
+  const size_t fixed = ((b_bytes + 1023) / 1024) * 1024 + ((x_bytes + 1023) / 1024) * 1024 + 512;
+  if (fixed >= limit) return 0;
+  int sa = (int)((limit - fixed) / a_stage);
+  sa = sa >= 8 ? 8 : sa >= 4 ? 4 : sa >= 2 ? 2 : 0;     // a power of two
+  if (sa < 2) return 0;
+  P.stages_a = sa;
+  P.off_b = (size_t)sa * a_stage;
+  P.off_x = P.off_b + ((b_bytes + 1023) / 1024) * 1024;
+  P.off_bar = (P.off_x + x_bytes + 15) / 16 * 16;
+  const size_t smem = P.off_bar + (size_t)(2 * sa + 2 * kMaxBSlots + 10) * 8 + 16;
+  // every descriptor footprint stays inside its stage: A parts are 128 rows x
+  // 64 B; a B piece [r0, r0 + w) ends at the end of its part
+  if ((size_t)15 * 512 + 256 + 255 >= (size_t)kPartBytes) return 0;
+  return smem <= limit ? smem : 0;
+}
+
+int num_sms() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
 }
 
 }  // namespace
 
+TcSess tc_session(const DevView& v, int n) {
+  TcSess S{};
+  S.codes = v.codes;
+  S.vtab32 = v.vtab32;
+  S.visited = v.visited;
+  S.xf = v.Xf;
+  S.rowq = v.rowq;
+  S.rowb = v.rowb;
+  S.lhi = v.lsplit_hi;
+  S.llo = v.lsplit_lo;
+  S.mu = static_cast<float*>(v.mu);
+  S.var = static_cast<float*>(v.var);
+  S.N = v.N;
+  S.N_pad = v.N_pad;
+  S.d = v.d;
+  S.n = n;
+  S.n_pad = (n + 31) / 32 * 32;
+  S.n_max = v.n_max;
+  S.chunks = S.n_pad / (kChunkBytes / (v.precision == BO_PREC_TF32 ? 4 : 2));
+  S.num_tiles = (int)(v.N_pad / kRows);
+  return S;
+}
+
 int launch_predict_tc(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStream_t s) {
   if (n < 1 || n > v.n_max || v.precision == BO_PREC_FP64 || v.d > 16) return -1;
-  TcParams P;
-  P.v = v;
-  P.n = n;
-  const int eb = v.precision == BO_PREC_TF32 ? 4 : 2;
-  P.cw = kChunkBytes / eb;
-  P.parts = v.precision == BO_PREC_TF32 ? 1 : 2;
-  P.n_pad = (n + 31) / 32 * 32;
-  if (P.n_pad > v.n_max) return -1;
-  P.chunks = P.n_pad / P.cw;
-  int cols = 32;
-  while (cols < P.n_pad) cols <<= 1;
-  if (cols > 512) return -1;
-  P.tmem_cols = cols;
-  P.acc_stages = 2 * cols <= 512 ? 2 : 1;
-  P.num_tiles = (int)(v.N_pad / kRows);
-  // shared memory plan
-  const size_t a_stage = (size_t)P.parts * kPartBytes;
-  const size_t x_bytes = (size_t)dim_bucket(v.d) * P.n_pad * 4;
-  const size_t q_bytes = (size_t)2 * P.n_pad * 4;
-  const size_t limit = 226 * 1024;   // dynamic part; the kernel's static shared memory is small
-  size_t resident = 0;
-  int pieces = 0;
-  for (int c = 0; c < P.chunks; ++c)
-    for (int r0 = c * P.cw; r0 < P.n_pad; r0 += kPieceRows, ++pieces)
-      resident += (size_t)P.parts * (std::min(kPieceRows, P.n_pad - r0) / 8) * 512;
-  P.b_resident = (pieces <= kMaxBSlots && resident <= (size_t)P.parts * 64 * 1024) ? 1 : 0;
-  P.b_slots = 4;
-  P.b_slot_bytes = (size_t)P.parts * (kPieceRows / 8) * 512;
-  const size_t b_bytes = P.b_resident ? resident : P.b_slots * P.b_slot_bytes;
-  const size_t fixed = ((b_bytes + 1023) / 1024) * 1024 + ((x_bytes + q_bytes + 1023) / 1024) * 1024 + 512;
-  int sa = (int)((limit - fixed) / a_stage);
-  sa = sa >= 8 ? 8 : sa >= 4 ? 4 : sa >= 2 ? 2 : 0;     // a power of two
-  if (sa < 2) return -1;
-  P.stages_a = sa;
-  P.off_b = (size_t)sa * a_stage;
-  P.off_x = P.off_b + ((b_bytes + 1023) / 1024) * 1024;
-  P.off_q = P.off_x + x_bytes;
-  P.off_bar = (P.off_q + q_bytes + 15) / 16 * 16;
-  const size_t smem = P.off_bar + (size_t)(2 * sa + 2 * kMaxBSlots + 6) * 8 + 16;
-  if (smem > limit) return -1;
-  // every descriptor footprint stays inside its stage: A parts are 128 rows x
-  // 64 B; a B piece [n0, n0 + w) of chunk c ends at row n_pad - c*cw of its part
-  if ((size_t)15 * 512 + 256 + 255 >= (size_t)kPartBytes) return -1;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = P.num_tiles < sms ? P.num_tiles : sms;
+  TcParams P{};
+  P.s0 = tc_session(v, n);
+  if (P.s0.n_pad > v.n_max) return -1;
+  P.batch = 0;
+  P.xs_bufs = 1;
+  P.partial = v.partial;
+  P.stats = v.stats;
+  P.status = &v.stats->status;
+  const int dmax = dim_bucket(v.d);
+  const size_t smem = plan_smem(P, v.precision, P.s0.n_pad, dmax, true);
+  if (!smem) return -1;
+  const int grid = std::min(P.s0.num_tiles, num_sms());
   if (grid > v.max_partials) return -1;
-  switch (v.precision) {
-    case BO_PREC_FP16X3: return launch_nu<BO_PREC_FP16X3>(P, smem, grid, s);
-    case BO_PREC_BF16X3: return launch_nu<BO_PREC_BF16X3>(P, smem, grid, s);
-    default: return launch_nu<BO_PREC_TF32>(P, smem, grid, s);
-  }
+  return dispatch(P, v.precision, v.nu, dmax, smem, grid, s);
 }
+
+int tc_plan_batch(const TcSess* sess, int count, int dmax, int grid, std::vector<TcSeg>* segs,
+                  std::vector<int>* seg_begin) {
+  // estimated cost of one tile of space s: K* production ~ n_pad (dmax + 12)
+  // lane-operations per row, contraction ~ 3 n_pad^2 / 2 MACs at ~32 per lane-op
+  std::vector<double> tile_cost(count);
+  double total = 0.0;
+  for (int s = 0; s < count; ++s) {
+    const double np = sess[s].n_pad;
+    tile_cost[s] = np * (1.25 * dmax + 12.0) + 3.0 * np * np / 64.0;
+    total += tile_cost[s] * sess[s].num_tiles;
+  }
+  segs->clear();
+  seg_begin->assign(grid + 1, 0);
+  int s = 0, t = 0;
+  double acc = 0.0;
+  for (int b = 0; b < grid; ++b) {
+    (*seg_begin)[b] = (int)segs->size();
+    const double goal = total * (b + 1) / grid;
+    while (s < count) {
+      if (t >= sess[s].num_tiles) { ++s; t = 0; continue; }
+      // whole tiles of space s until this CTA's share is reached (the last CTA takes the rest)
+      int take = sess[s].num_tiles - t;
+      if (b + 1 < grid) {
+        const double room = goal - acc;
+        const int fit = (int)(room / tile_cost[s] + 0.5);
+        take = std::min(take, std::max(fit, 0));
+      }
+      if (take <= 0) break;
+      segs->push_back(TcSeg{s, t, t + take});
+      acc += take * tile_cost[s];
+      t += take;
+      if (t < sess[s].num_tiles) break;
+    }
+  }
+  (*seg_begin)[grid] = (int)segs->size();
+  return (int)segs->size();
+}
+
+int launch_predict_tc_batch(const TcBatchLaunch& L, cudaStream_t s) {
+  if (L.count < 1 || L.precision == BO_PREC_FP64) return -1;
+  TcParams P{};
+  P.batch = L.count;
+  P.sess = L.sess;
+  P.segs = L.segs;
+  P.seg_begin = L.seg_begin;
+  P.seg_part = L.seg_part;
+  P.status = L.status;
+  P.xs_bufs = 2;
+  const size_t smem = plan_smem(P, L.precision, L.n_pad_max, L.dmax, false);
+  if (!smem) return -1;
+  return dispatch(P, L.precision, L.nu, L.dmax, smem, L.grid, s);
+}
+
+int tc_dim_bucket(int d) { return dim_bucket(d); }
 
 }  // namespace bo

@@ -16,13 +16,19 @@
 #include <string>
 #include <vector>
 
-#include "bo_internal.h"
+#include "bo_space_impl.h"
 
 using namespace bo;
+using namespace bo::host;
 
 namespace {
 
 thread_local std::string g_err;
+
+}  // namespace
+
+namespace bo {
+namespace host {
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -38,12 +44,6 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(BO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define BO_CUDA(call)                                  \
-  do {                                                 \
-    cudaError_t e_ = (call);                           \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
-
 // splitmix64 (Steele, Lea and Flood 2014), from its published definition.
 uint64_t splitmix64_next(uint64_t& state) {
   state += 0x9E3779B97F4A7C15ull;
@@ -53,135 +53,11 @@ uint64_t splitmix64_next(uint64_t& state) {
   return z ^ (z >> 31);
 }
 
-struct Pick {
-  int64_t idx;
-  std::vector<int> afs;
-  double mu, sigma, score;
-};
+}  // namespace host
+}  // namespace bo
 
-// Selection of acquisition functions (paper Sec. III-G, Table I).
-//   single:   one AF, one pick per pass.
-//   multi:    every active AF picks from one shared pass; each pair of AFs
-//             with the same pick gains a duplicate each and becomes partners
-//             (the pick is evaluated once, credited to both); at the start of
-//             a round an AF whose count exceeds the threshold is pitted with
-//             its partners and only the lowest dos among them stays.
-//   advanced: an AF picks its best candidate not taken by an earlier AF in
-//             the round; each round after the first, dos above mean*(1+rif)
-//             counts 'over', below mean*(1-rif) counts 'under' (cumulative);
-//             an 'under' count at the threshold promotes that AF to be the
-//             only one, else an 'over' count at it skips the AF and resets
-//             the others' counts.
-// dos <- gamma * dos + o for every observation credited to an AF.
-struct Selector {
-  int mode = BO_AF_EI;
-  std::vector<int> active;
-  double dos[3] = {0, 0, 0};
-  int dup[3] = {0, 0, 0};
-  unsigned partners[3] = {0, 0, 0};
-  int over[3] = {0, 0, 0}, under[3] = {0, 0, 0};
-  int rounds = 0;
-  int threshold = 5;
-  double gamma = 0.65, rif = 0.1;
-
-  void init(int m, int thr, double discount, double r) {
-    mode = m;
-    threshold = thr;
-    rif = r;
-    if (m == BO_AF_MULTI || m == BO_AF_ADV_MULTI) {
-      active = {kEI, kPI, kLCB};
-      gamma = discount > 0 ? discount : (m == BO_AF_MULTI ? 0.65 : 0.75);
-    } else {
-      active = {m};
-    }
-  }
-
-  bool is_active(int a) const {
-    return std::find(active.begin(), active.end(), a) != active.end();
-  }
-
-  void begin_round() {
-    if (mode == BO_AF_MULTI && rounds > 0) {
-      unsigned group = 0;
-      for (int a : active)
-        if (dup[a] > threshold) group |= (1u << a) | partners[a];
-      if (group) {
-        int keep = -1;
-        for (int a = 0; a < 3; ++a)   // AF ids are in Table I order
-          if ((group >> a & 1u) && is_active(a) && (keep < 0 || dos[a] < dos[keep])) keep = a;
-        std::vector<int> next;
-        for (int a : active)
-          if (!(group >> a & 1u) || a == keep) next.push_back(a);
-        active = next;
-        for (int a = 0; a < 3; ++a) { dup[a] = 0; partners[a] = 0; }
-      }
-    } else if (mode == BO_AF_ADV_MULTI && rounds > 0 && active.size() >= 2) {
-      double m = 0;
-      for (int a : active) m += dos[a];
-      m /= (double)active.size();
-      for (int a : active) {
-        if (dos[a] > m * (1.0 + rif)) ++over[a];
-        else if (dos[a] < m * (1.0 - rif)) ++under[a];
-      }
-      int promote = -1, skip = -1;
-      for (int a : active)
-        if (promote < 0 && under[a] >= threshold) promote = a;
-      for (int a : active)
-        if (skip < 0 && over[a] >= threshold) skip = a;
-      if (promote >= 0) {
-        active = {promote};
-      } else if (skip >= 0) {
-        active.erase(std::find(active.begin(), active.end(), skip));
-        for (int a : active) over[a] = under[a] = 0;
-      }
-    }
-    ++rounds;
-  }
-
-  // picks of one round from the pass result, whose AF rows follow `active`
-  std::vector<Pick> assign(const bo_pass_result& r) {
-    std::vector<Pick> picks;
-    for (size_t q = 0; q < active.size(); ++q) {
-      const int a = active[q];
-      if (mode == BO_AF_ADV_MULTI) {
-        for (int k = 0; k < 3; ++k) {
-          const int64_t i = r.top_idx[q][k];
-          if (i < 0) break;
-          bool taken = false;
-          for (auto& p : picks) taken |= (p.idx == i);
-          if (!taken) {
-            picks.push_back({i, {a}, r.top_mu[q][k], r.top_sigma[q][k], r.top_score[q][k]});
-            break;
-          }
-        }
-        continue;
-      }
-      const int64_t i = r.top_idx[q][0];
-      if (i < 0) continue;
-      Pick* same = nullptr;
-      for (auto& p : picks)
-        if (p.idx == i) same = &p;
-      if (same && mode == BO_AF_MULTI) {
-        for (int b : same->afs) {
-          ++dup[a];
-          ++dup[b];
-          partners[a] |= 1u << b;
-          partners[b] |= 1u << a;
-        }
-        same->afs.push_back(a);
-      } else if (!same) {
-        picks.push_back({i, {a}, r.top_mu[q][0], r.top_sigma[q][0], r.top_score[q][0]});
-      }
-    }
-    return picks;
-  }
-
-  void credit(const std::vector<int>& afs, double value) {
-    if (mode != BO_AF_MULTI && mode != BO_AF_ADV_MULTI) return;
-    for (int a : afs) dos[a] = gamma * dos[a] + value;
-  }
-};
-
+namespace {
+using bo::host::Pick;
 }  // namespace
 
 int bo::report_error(int code, const char* msg) {
@@ -189,37 +65,9 @@ int bo::report_error(int code, const char* msg) {
   return code;
 }
 
-struct bo_space {
-  bo_space_desc desc;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int d = 0;
-  std::vector<int> sizes;
-  std::vector<std::vector<double>> values;
-  int64_t N = 0;
-  std::vector<uint8_t> codes;        // [d][N] host copy
-  std::vector<uint8_t> visited;      // [N]
-  int64_t n_visited = 0;
-  std::vector<int64_t> obs_idx;
-  std::vector<double> obs_y;
-  std::vector<double> fit_y;         // finite observations in fit order
-  int n_fit = 0;
-  int n_cap = 0;                     // desc.n_max
-  bool cv_set = false;
-  double mu_s = 0;
-  uint64_t rng = 0;
-  Selector sel;
-  std::deque<Pick> queue;
-  std::map<int64_t, std::vector<int>> outstanding;
-  DevView v{};
-  std::vector<std::pair<void*, size_t>> blocks;
-  bo_pass_result* host_result = nullptr;   // pinned
-  int64_t launches = 0;
-  int replay_steps = 0;
-  int poisoned = BO_OK;
-};
 
-namespace {
+namespace bo {
+namespace host {
 
 int dalloc(bo_space* s, size_t bytes, void** out) {
   bytes = std::max<size_t>(bytes, 256);
@@ -278,7 +126,7 @@ double median(std::vector<double> a) {
   return n % 2 ? a[n / 2] : 0.5 * (a[n / 2 - 1] + a[n / 2]);
 }
 
-int launch_pass(bo_space* s, const std::vector<int>& afs, int slot) {
+int prepare_pass(bo_space* s, const std::vector<int>& afs, int slot, PassArgs* out) {
   PassArgs a{};
   a.n = s->n_fit;
   a.n_unvisited = s->N - s->n_visited;
@@ -308,6 +156,14 @@ int launch_pass(bo_space* s, const std::vector<int>& afs, int slot) {
     if (!s->cv_set) { s->mu_s = mu_s; s->cv_set = true; }
   }
   a.result_slot = slot;
+  *out = a;
+  return BO_OK;
+}
+
+int launch_pass(bo_space* s, const std::vector<int>& afs, int slot) {
+  PassArgs a;
+  const int rc = prepare_pass(s, afs, slot, &a);
+  if (rc != BO_OK) return rc;
   const int k1 = s->desc.precision == BO_PREC_FP64
                      ? launch_predict_f64(s->v, s->n_fit, a.n_unvisited, s->stream)
                      : launch_predict_tc(s->v, s->n_fit, a.n_unvisited, s->stream);
@@ -324,6 +180,7 @@ int fetch_result(bo_space* s, int slot) {
   BO_CUDA(cudaMemcpyAsync(s->host_result, s->v.results + slot, sizeof(bo_pass_result),
                           cudaMemcpyDeviceToHost, s->stream));
   BO_CUDA(cudaStreamSynchronize(s->stream));
+  s->last = *s->host_result;
   if (s->host_result->status != BO_OK) {
     s->poisoned = s->host_result->status;
     return fail(s->poisoned, "device reported status %d (non-positive pivot or non-finite posterior)",
@@ -332,7 +189,8 @@ int fetch_result(bo_space* s, int slot) {
   return BO_OK;
 }
 
-int observe_impl(bo_space* s, int64_t idx, double value) {
+int observe_host(bo_space* s, int64_t idx, double value, bool* fit, int* n_before, double* y_mean,
+                 double* y_std) {
   if (idx < 0 || idx >= s->N) return fail(BO_ERR_INDEX, "index %lld out of range [0, %lld)",
                                           (long long)idx, (long long)s->N);
   if (s->visited[idx]) return fail(BO_ERR_DUPLICATE, "configuration %lld already observed",
@@ -344,18 +202,14 @@ int observe_impl(bo_space* s, int64_t idx, double value) {
   ++s->n_visited;
   s->obs_idx.push_back(idx);
   s->obs_y.push_back(value);
-  int k;
+  *fit = finite;
+  *n_before = s->n_fit;
   if (finite) {
     s->fit_y.push_back(value);
-    double mean, sd, ymin;
-    y_stats(s, &mean, &sd, &ymin);
-    k = launch_observe_update(s->v, s->n_fit, idx, value, mean, sd, s->stream);
+    double ymin;
+    y_stats(s, y_mean, y_std, &ymin);
     ++s->n_fit;
-  } else {
-    k = launch_set_visited(s->v, idx, s->stream);
   }
-  if (k < 0) return fail(BO_ERR_CUDA, "update launch failed");
-  s->launches += k;
   auto it = s->outstanding.find(idx);
   if (it != s->outstanding.end()) {
     if (finite) s->sel.credit(it->second, value);
@@ -365,7 +219,88 @@ int observe_impl(bo_space* s, int64_t idx, double value) {
   return BO_OK;
 }
 
-}  // namespace
+int observe_impl(bo_space* s, int64_t idx, double value) {
+  bool fit = false;
+  int n_before = 0;
+  double mean = 0.0, sd = 1.0;
+  int rc = observe_host(s, idx, value, &fit, &n_before, &mean, &sd);
+  if (rc != BO_OK) return rc;
+  const int k = fit ? launch_observe_update(s->v, n_before, idx, value, mean, sd, s->stream)
+                    : launch_set_visited(s->v, idx, s->stream);
+  if (k < 0) return fail(BO_ERR_CUDA, "update launch failed");
+  s->launches += k;
+  return BO_OK;
+}
+
+int suggest_begin(bo_space* s, int64_t* idx_out, bo_suggest_info* info, bool* need_pass) {
+  *need_pass = false;
+  bo_suggest_info inf{};
+  inf.af = -1;
+  if (s->n_visited >= s->N) return fail(BO_ERR_EXHAUSTED, "every valid configuration was evaluated");
+  if ((int64_t)s->obs_y.size() < s->desc.n_init || s->n_fit == 0) {
+    const int64_t free_count = s->N - s->n_visited;
+    int64_t r = (int64_t)(splitmix64_next(s->rng) % (uint64_t)free_count);
+    int64_t idx = -1;
+    for (int64_t i = 0; i < s->N; ++i)
+      if (!s->visited[i] && r-- == 0) { idx = i; break; }
+    inf.idx = idx;
+    *idx_out = idx;
+    if (info) *info = inf;
+    return BO_OK;
+  }
+  while (!s->queue.empty()) {
+    Pick p = s->queue.front();
+    s->queue.pop_front();
+    if (s->visited[p.idx]) continue;
+    s->outstanding[p.idx] = p.afs;
+    inf.idx = p.idx;
+    inf.af = p.afs[0];
+    inf.predicted = 1;
+    inf.mu = p.mu;
+    inf.sigma = p.sigma;
+    inf.score = p.score;
+    inf.lambda = s->last.lambda;
+    inf.mean_var = s->last.mean_var;
+    inf.n_scored = 0;
+    *idx_out = p.idx;
+    if (info) *info = inf;
+    return BO_OK;
+  }
+  s->sel.begin_round();
+  s->outstanding.clear();
+  *need_pass = true;
+  return BO_OK;
+}
+
+int suggest_finish(bo_space* s, const bo_pass_result& r, int64_t* idx_out, bo_suggest_info* info) {
+  s->last = r;
+  if (r.status != BO_OK) {
+    s->poisoned = r.status;
+    return fail(r.status, "device reported status %d (non-positive pivot, non-finite posterior or timeout)",
+                r.status);
+  }
+  std::vector<Pick> picks = s->sel.assign(r);
+  if (picks.empty()) return fail(BO_ERR_EXHAUSTED, "no pick available");
+  s->queue.assign(picks.begin() + 1, picks.end());
+  const Pick& p = picks[0];
+  s->outstanding[p.idx] = p.afs;
+  bo_suggest_info inf{};
+  inf.idx = p.idx;
+  inf.af = p.afs[0];
+  inf.predicted = 1;
+  inf.mu = p.mu;
+  inf.sigma = p.sigma;
+  inf.score = p.score;
+  inf.lambda = r.lambda;
+  inf.mean_var = r.mean_var;
+  inf.n_scored = r.n_scored;
+  *idx_out = p.idx;
+  if (info) *info = inf;
+  return BO_OK;
+}
+
+}  // namespace host
+}  // namespace bo
 
 extern "C" {
 
@@ -483,7 +418,7 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   TRY(dalloc_n(s, (size_t)D.d * 256, &vt32));
   TRY(dalloc_n(s, (size_t)N_pad / 32 + 1, &v.visited));
   TRY(dalloc_n(s, (size_t)n_alloc * D.d, &v.X));
-  TRY(dalloc_n(s, (size_t)n_alloc * D.d, &v.Xf));
+  TRY(dalloc_n(s, (size_t)kXfRows * n_alloc, &v.Xf));
   TRY(dalloc_n(s, (size_t)n_alloc, &v.y));
   TRY(dalloc_n(s, (size_t)n_alloc * n_alloc, &v.linv));
   TRY(dalloc_n(s, (size_t)n_alloc, &v.beta));
@@ -558,60 +493,32 @@ int bo_suggest(bo_space* s, int64_t* idx_out, bo_suggest_info* info) {
   if (!s || !idx_out) return fail(BO_ERR_ARG, "null argument");
   if (s->poisoned) return fail(s->poisoned, "space is unusable after an earlier numeric failure");
   cudaSetDevice(s->device);
-  bo_suggest_info inf{};
-  inf.af = -1;
-  if (s->n_visited >= s->N) return fail(BO_ERR_EXHAUSTED, "every valid configuration was evaluated");
-  if ((int64_t)s->obs_y.size() < s->desc.n_init || s->n_fit == 0) {
-    const int64_t free_count = s->N - s->n_visited;
-    int64_t r = (int64_t)(splitmix64_next(s->rng) % (uint64_t)free_count);
-    int64_t idx = -1;
-    for (int64_t i = 0; i < s->N; ++i)
-      if (!s->visited[i] && r-- == 0) { idx = i; break; }
-    inf.idx = idx;
-    *idx_out = idx;
-    if (info) *info = inf;
-    return BO_OK;
-  }
-  while (!s->queue.empty()) {
-    Pick p = s->queue.front();
-    s->queue.pop_front();
-    if (s->visited[p.idx]) continue;
-    s->outstanding[p.idx] = p.afs;
-    inf.idx = p.idx;
-    inf.af = p.afs[0];
-    inf.predicted = 1;
-    inf.mu = p.mu;
-    inf.sigma = p.sigma;
-    inf.score = p.score;
-    inf.lambda = s->host_result->lambda;
-    inf.mean_var = s->host_result->mean_var;
-    inf.n_scored = 0;
-    *idx_out = p.idx;
-    if (info) *info = inf;
-    return BO_OK;
-  }
-  s->sel.begin_round();
-  s->outstanding.clear();
-  int rc = launch_pass(s, s->sel.active, 0);
+  bool need_pass = false;
+  int rc = suggest_begin(s, idx_out, info, &need_pass);
+  if (rc != BO_OK || !need_pass) return rc;
+  rc = launch_pass(s, s->sel.active, 0);
   if (rc != BO_OK) return rc;
-  rc = fetch_result(s, 0);
-  if (rc != BO_OK) return rc;
-  std::vector<Pick> picks = s->sel.assign(*s->host_result);
-  if (picks.empty()) return fail(BO_ERR_EXHAUSTED, "no pick available");
-  s->queue.assign(picks.begin() + 1, picks.end());
-  const Pick& p = picks[0];
-  s->outstanding[p.idx] = p.afs;
-  inf.idx = p.idx;
-  inf.af = p.afs[0];
-  inf.predicted = 1;
-  inf.mu = p.mu;
-  inf.sigma = p.sigma;
-  inf.score = p.score;
-  inf.lambda = s->host_result->lambda;
-  inf.mean_var = s->host_result->mean_var;
-  inf.n_scored = s->host_result->n_scored;
-  *idx_out = p.idx;
-  if (info) *info = inf;
+  BO_CUDA(cudaMemcpyAsync(s->host_result, s->v.results, sizeof(bo_pass_result), cudaMemcpyDeviceToHost,
+                          s->stream));
+  BO_CUDA(cudaStreamSynchronize(s->stream));
+  return suggest_finish(s, *s->host_result, idx_out, info);
+}
+
+int bo_last_posterior(bo_space* s, int64_t begin, int64_t count, double* mu_out, double* var_out) {
+  if (!s || (!mu_out && !var_out)) return fail(BO_ERR_ARG, "null argument");
+  if (begin < 0 || count < 0 || begin + count > s->N) return fail(BO_ERR_INDEX, "range out of bounds");
+  cudaSetDevice(s->device);
+  const size_t eb = s->desc.precision == BO_PREC_FP64 ? 8 : 4;
+  std::vector<uint8_t> tmp((size_t)count * eb);
+  for (int w = 0; w < 2; ++w) {
+    double* dst = w ? var_out : mu_out;
+    if (!dst) continue;
+    const uint8_t* src = static_cast<const uint8_t*>(w ? s->v.var : s->v.mu) + (size_t)begin * eb;
+    BO_CUDA(cudaMemcpyAsync(tmp.data(), src, (size_t)count * eb, cudaMemcpyDeviceToHost, s->stream));
+    BO_CUDA(cudaStreamSynchronize(s->stream));
+    for (int64_t i = 0; i < count; ++i)
+      dst[i] = eb == 8 ? reinterpret_cast<const double*>(tmp.data())[i] : reinterpret_cast<const float*>(tmp.data())[i];
+  }
   return BO_OK;
 }
 

@@ -57,15 +57,15 @@ size_t lsplit_bytes(int n_max, int precision) {
 }
 
 // --- K3a: X[n] = x(idx), y[n] = y, visited bit, k_j = k(|x - X_j|) --------------
-__global__ void obs_k_kernel(DevView v, int n, long long idx, double y_raw) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void obs_k_body(const DevView& v, int n, long long idx, double y_raw, int block) {
+  const int j = block * blockDim.x + threadIdx.x;
   const double c = sqrt(2.0 * v.nu) / v.lengthscale;
-  if (blockIdx.x == 0 && threadIdx.x < v.d) {
+  if (block == 0 && threadIdx.x < v.d) {
     const double x = coord64(v, idx, threadIdx.x);
     v.X[(size_t)n * v.d + threadIdx.x] = x;
-    v.Xf[(size_t)n * v.d + threadIdx.x] = (float)(x * (1.4426950408889634 * c));
+    v.Xf[(size_t)threadIdx.x * v.n_max + n] = (float)(x * (1.4426950408889634 * c));
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (block == 0 && threadIdx.x == 0) {
     v.y[n] = y_raw;
     atomicOr(&v.visited[idx >> 5], 1u << (idx & 31));
   }
@@ -79,14 +79,18 @@ __global__ void obs_k_kernel(DevView v, int n, long long idx, double y_raw) {
   }
 }
 
+__global__ void obs_k_kernel(DevView v, int n, long long idx, double y_raw) {
+  obs_k_body(v, n, idx, y_raw, blockIdx.x);
+}
+
 __device__ __forceinline__ double warp_sum(double x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
 
 // --- K3b: l = L^-1 k (warp per row) -------------------------------------------
-__global__ void obs_l_kernel(DevView v, int n) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void obs_l_body(const DevView& v, int n, int block) {
+  const int warp = (block * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
   const double* row = v.linv + (size_t)warp * v.n_max;
@@ -97,14 +101,16 @@ __global__ void obs_l_kernel(DevView v, int n) {
   if (lane == 0) v.lvec[warp] = s;
 }
 
+__global__ void obs_l_kernel(DevView v, int n) { obs_l_body(v, n, blockIdx.x); }
+
 // --- K3c: partial w = L^-T l over row segments of 64 ---------------------------
 // Block (column block of 32, row segment of 64): lane = column, warp w sums
 // rows seg*64 + 8w .. +8 with all eight loads in flight; L^-1[i][j] = 0 for j > i.
-__global__ void obs_w_kernel(DevView v, int n) {
+__device__ __forceinline__ void obs_w_body(const DevView& v, int n, int bx, int by) {
   __shared__ double part[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int j = blockIdx.x * 32 + lane;
-  const int i0 = blockIdx.y * 64 + w * 8;
+  const int j = bx * 32 + lane;
+  const int i0 = by * 64 + w * 8;
   double s = 0.0;
   if (j < n) {
     double a[8], b[8];
@@ -124,12 +130,14 @@ __global__ void obs_w_kernel(DevView v, int n) {
     double t = 0.0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) t += part[q][lane];
-    v.wvec[(size_t)blockIdx.y * v.n_max + j] = t;
+    v.wvec[(size_t)by * v.n_max + j] = t;
   }
 }
 
+__global__ void obs_w_kernel(DevView v, int n) { obs_w_body(v, n, blockIdx.x, blockIdx.y); }
+
 // --- K3d: pivot, new row n of L^-1 and its split copy (one block) --------------
-__global__ void obs_finish_kernel(DevView v, int n) {
+__device__ __forceinline__ void obs_finish_body(const DevView& v, int n) {
   __shared__ double red[32];
   __shared__ double s_dinv;
   __shared__ float s_scale;
@@ -204,9 +212,13 @@ __global__ void obs_finish_kernel(DevView v, int n) {
   }
 }
 
+__global__ void obs_finish_kernel(DevView v, int n) { obs_finish_body(v, n); }
+
+
 // --- K3e: beta = L^-1 y~ for rows 0..n, and beta_k / s_k -------------------------
-__global__ void obs_beta_kernel(DevView v, int rows, double y_mean, double inv_std) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void obs_beta_body(const DevView& v, int rows, double y_mean, double inv_std,
+                                              int block) {
+  const int warp = (block * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= rows) return;
   const double* row = v.linv + (size_t)warp * v.n_max;
@@ -219,8 +231,85 @@ __global__ void obs_beta_kernel(DevView v, int rows, double y_mean, double inv_s
   }
 }
 
+__global__ void obs_beta_kernel(DevView v, int rows, double y_mean, double inv_std) {
+  obs_beta_body(v, rows, y_mean, inv_std, blockIdx.x);
+}
+
+// ---- the same phases over many spaces: block b serves item blocks[b].item ----
+__global__ void obs_k_batch(const ObsItem* items, const ObsBlock* blocks) {
+  const ObsBlock b = blocks[blockIdx.x];
+  const ObsItem& it = items[b.item];
+  obs_k_body(it.v, it.n, it.idx, it.y_raw, b.local);
+}
+
+__global__ void obs_l_batch(const ObsItem* items, const ObsBlock* blocks) {
+  const ObsBlock b = blocks[blockIdx.x];
+  const ObsItem& it = items[b.item];
+  obs_l_body(it.v, it.n, b.local);
+}
+
+__global__ void obs_w_batch(const ObsItem* items, const ObsBlock* blocks) {
+  const ObsBlock b = blocks[blockIdx.x];
+  const ObsItem& it = items[b.item];
+  const int gx = (it.n + 31) / 32;
+  obs_w_body(it.v, it.n, b.local % gx, b.local / gx);
+}
+
+__global__ void obs_finish_batch(const ObsItem* items) {
+  const ObsItem& it = items[blockIdx.x];
+  obs_finish_body(it.v, it.n);
+}
+
+__global__ void obs_beta_batch(const ObsItem* items, const ObsBlock* blocks) {
+  const ObsBlock b = blocks[blockIdx.x];
+  const ObsItem& it = items[b.item];
+  obs_beta_body(it.v, it.n + 1, it.y_mean, it.inv_std, b.local);
+}
+
+__global__ void set_visited_batch(const VisitItem* items, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) atomicOr(&items[i].visited[items[i].idx >> 5], 1u << (items[i].idx & 31));
+}
+
 __global__ void set_visited_kernel(uint32_t* visited, long long idx) {
   atomicOr(&visited[idx >> 5], 1u << (idx & 31));
+}
+
+void obs_batch_blocks(const int* n, int count, std::vector<ObsBlock>* blocks, int counts[4]) {
+  // per phase, the blocks each space needs (as the single-space launch uses)
+  blocks->clear();
+  auto add = [&](int phase_blocks(int), int slot) {
+    const size_t start = blocks->size();
+    for (int i = 0; i < count; ++i)
+      for (int b = 0; b < phase_blocks(n[i]); ++b) blocks->push_back(ObsBlock{i, b});
+    counts[slot] = (int)(blocks->size() - start);
+  };
+  add([](int m) { return (m + 31) / 32 + (m == 0); }, 0);             // k: 32 threads
+  add([](int m) { return (m + 7) / 8; }, 1);                          // l: warp per row
+  add([](int m) { return ((m + 31) / 32) * ((m + 63) / 64); }, 2);    // w: 32 columns x 64 rows
+  add([](int m) { return (m + 1 + 7) / 8; }, 3);                      // beta: warp per row
+}
+
+int launch_observe_batch(const ObsItem* items, int count, const ObsBlock* blocks, const int counts[4],
+                         const VisitItem* visits, int n_visits, cudaStream_t s) {
+  int launches = 0;
+  const ObsBlock* b = blocks;
+  if (count > 0) {
+    if (counts[0]) { obs_k_batch<<<counts[0], 32, 0, s>>>(items, b); ++launches; }
+    b += counts[0];
+    if (counts[1]) { obs_l_batch<<<counts[1], 256, 0, s>>>(items, b); ++launches; }
+    b += counts[1];
+    if (counts[2]) { obs_w_batch<<<counts[2], 256, 0, s>>>(items, b); ++launches; }
+    b += counts[2];
+    obs_finish_batch<<<count, 512, 0, s>>>(items);
+    ++launches;
+    if (counts[3]) { obs_beta_batch<<<counts[3], 256, 0, s>>>(items, b); ++launches; }
+  }
+  if (n_visits > 0) {
+    set_visited_batch<<<(n_visits + 127) / 128, 128, 0, s>>>(visits, n_visits);
+    ++launches;
+  }
+  return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
 int launch_set_visited(const DevView& v, int64_t idx, cudaStream_t s) {
