@@ -247,6 +247,143 @@ def measure_device(cfg_id, precision, steps, warm, flush, stream):
                 k1=statistics.median(k1), value=scored / sum(times))
 
 
+def batched_workload(count, steps, warm, precision, seed=0):
+    """Sessions of the batched configuration: d ~ U{3..9}, N ~ log-U[1k, 500k],
+    final n ~ U{20..400}; the last warm + steps observations of each session
+    are held back for the timed steps."""
+    from paper_2111_14991_gb300 import Batch, Space
+    from paper_2111_14991_gb300 import workloads as W
+    sps = W.batched_spaces(count, seed=seed)
+    spaces, obs = [], []
+    n_max = min(512, max(sp.meta["n_obs"] for sp in sps) + 1)
+    for sp in sps:
+        land = W.Landscape(sp, sp.meta["session"])
+        idx = W.clustered_observations(land, sp.meta["n_obs"], sp.meta["session"])
+        obs.append((idx, land.clean(idx)))
+        spaces.append(Space(sp.grids, sp.invalid, precision=precision, af="ei", n_max=n_max))
+    batch = Batch(spaces)
+    hold = warm + steps
+    rounds = max(len(i) for i, _ in obs) - hold
+    for r in range(rounds):                      # initial observations, one batched update per round
+        ii = [int(i[r]) if r < len(i) - hold else -1 for i, _ in obs]
+        yy = [float(y[r]) if r < len(i) - hold else 0.0 for i, y in obs]
+        batch.observe(ii, yy)
+    return sps, spaces, batch, obs
+
+
+def measure_batched(count, steps, warm, precision, stream):
+    """Device-timed batched steps: one observation per session (batched update)
+    and one prediction pass per session (one persistent launch)."""
+    import torch
+    sps, spaces, batch, obs = batched_workload(count, steps, warm, precision)
+    hold = warm + steps
+    times, scored, flops = [], 0, 0.0
+    for t in range(warm + steps):
+        ii = [int(i[len(i) - hold + t]) for i, _ in obs]
+        yy = [float(y[len(y) - hold + t]) for _, y in obs]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = batch.launch_count()
+        e0.record(stream)
+        st = batch.observe(ii, yy)
+        idx, st2, info = batch.suggest()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert not st.any() and not st2.any(), (st, st2)
+        if t >= warm:
+            times.append(e0.elapsed_time(e1) / 1e3)
+            scored += sum(x["n_scored"] for x in info)
+            n_now = [len(i) - hold + t + 1 for i, _ in obs]
+            flops += sum(float(sp.n_valid) * n * (n + 1) for sp, n in zip(sps, n_now))
+    launches = batch.launch_count()
+    batch.close()
+    for sp in spaces:
+        sp.close()
+    return dict(value=scored / sum(times), times=times, flops=flops, sessions=count,
+                candidates=sum(sp.n_valid for sp in sps), launches=launches)
+
+
+def measure_serving(count, rate, duration, precision, extra=160, seed=0):
+    """Open-loop serving: Poisson arrivals at `rate` requests/s (observe one new
+    point + suggest) spread uniformly over `count` live sessions of the batched
+    configuration's sizes, for `duration` seconds; then a closed-loop run with
+    one request of every session always in flight (saturation)."""
+    import torch
+    from paper_2111_14991_gb300 import Server
+    from paper_2111_14991_gb300 import workloads as W
+    sps = W.batched_spaces(count, seed=seed)
+    srv = Server(budget_bytes=120 << 30, max_sessions=1024)
+    rng = np.random.default_rng(seed + 99)
+    sids, pending = [], []
+    for sp in sps:
+        land = W.Landscape(sp, sp.meta["session"])
+        init = W.clustered_observations(land, min(sp.meta["n_obs"], 512 - extra - 8), sp.meta["session"])
+        rest = np.setdiff1d(rng.choice(sp.n_valid, min(sp.n_valid, len(init) + extra), replace=False), init)
+        sid = srv.open(sp.grids, sp.invalid, precision=precision, af="ei", n_max=512)
+        for i, v in zip(init, land.clean(init)):
+            srv.submit(sid, int(i), float(v), suggest=False)
+        sids.append(sid)
+        pending.append(list(zip(rest.tolist(), land.clean(rest).tolist())))
+    n_warm = srv.stats()["requests"]
+    t_end = time.time() + 600
+    while srv.stats()["completed"] < n_warm and time.time() < t_end:
+        srv.poll(4096, wait_ms=20)
+    srv.poll(1 << 16, wait_ms=0)
+    # ---- open loop
+    n_req = int(rate * duration)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    who = rng.integers(0, count, size=n_req)
+    done, submitted = [], 0
+    t0 = srv.now()
+    for k in range(n_req):
+        while srv.now() - t0 < arrivals[k]:
+            done += srv.poll(4096, wait_ms=0)
+        s = int(who[k])
+        if pending[s]:
+            i, v = pending[s].pop()
+            srv.submit(sids[s], i, v, tag=k)
+            submitted += 1
+    t_end = time.time() + 120
+    while len(done) < submitted and time.time() < t_end:
+        done += srv.poll(4096, wait_ms=20)
+    lat = np.array([c["t_done"] - c["t_submit"] for c in done if c["idx"] >= 0])
+    span = max(c["t_done"] for c in done) - t0
+    scored = sum(c["info"]["n_scored"] for c in done if c["idx"] >= 0)
+    open_loop = {"requests": len(lat), "rate_req_s": rate, "duration_s": round(span, 3),
+                 "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                 "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                 "candidates_per_s": round(scored / span, 1)}
+    # ---- closed loop: every session keeps one request in flight
+    it0 = srv.stats()
+    t0 = srv.now()
+    inflight = 0
+    for s in range(count):
+        if pending[s]:
+            i, v = pending[s].pop()
+            srv.submit(sids[s], i, v, tag=s)
+            inflight += 1
+    scored, n_done, t_stop = 0, 0, t0 + duration
+    while inflight and srv.now() < t_stop:
+        for c in srv.poll(4096, wait_ms=5):
+            inflight -= 1
+            n_done += 1
+            scored += c["info"]["n_scored"]
+            s = sids.index(c["session"])
+            if pending[s]:
+                i, v = pending[s].pop()
+                srv.submit(sids[s], i, v, tag=s)
+                inflight += 1
+    span = srv.now() - t0
+    while inflight:
+        inflight -= len(srv.poll(4096, wait_ms=20))
+    st = srv.stats()
+    closed_loop = {"requests": n_done, "duration_s": round(span, 3), "candidates_per_s": round(scored / span, 1),
+                   "iterations": st["iterations"] - it0["iterations"]}
+    stats = srv.stats()
+    srv.close()
+    return {"sessions": count, "open_loop": open_loop, "closed_loop": closed_loop,
+            "admitted": stats["admitted"], "bytes_in_use": stats["bytes_in_use"]}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2111_14991_gb300 import Space, build
@@ -308,6 +445,23 @@ def run_ours(args, rank, world):
                 "ms_per_step": round(1e3 * sum(f["times"]) / len(f["times"]), 4),
                 "n_obs": f"{f['n0'] + 4}..{f['n_last']}",
                 "roofline": roofline_for(fprec, f["n_last"], f["sp"].d, f["sp"].n_valid, f["k1"])}
+        if not args.no_serving:
+            forms["config5/fp16x3-served"] = measure_serving(args.batch_sessions, 2000.0, 4.0, "fp16x3")
+        if not args.no_batched:
+            bsteps = max(3, min(steps, 10))
+            f = measure_batched(args.batch_sessions, bsteps, 3, "fp16x3", stream)
+            peak = _peaks()["bf16_tflops"]
+            ach = f["flops"] / sum(f["times"]) / 1e12
+            forms["config4/fp16x3-batched"] = {
+                "value": round(f["value"], 1), "unit": "candidates/s",
+                "ms_per_step": round(1e3 * sum(f["times"]) / len(f["times"]), 4),
+                "sessions": f["sessions"], "candidates": f["candidates"],
+                "what": "per step: one batched update + one batched prediction pass of every session",
+                "l2": "working set > L2 (no flush)",
+                "roofline": {"bound": "tensor", "kernel": "whole batched step", "achieved": round(ach, 2),
+                             "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                             "peak_source": "measured bf16 burst; step time bounds the kernel time from above",
+                             "traffic": None}}
 
     value, tot = aggregate(m["scored"], tot, world, "cuda")
     e2e_value, e2e_tot = aggregate(e2e_scored, e2e_tot, world, "cuda")
@@ -414,6 +568,9 @@ def main():
     ap.add_argument("--latency-reps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched (256-session) form")
+    ap.add_argument("--batch-sessions", type=int, default=256)
+    ap.add_argument("--no-serving", action="store_true", help="skip the served form")
     ap.add_argument("--kernel-only", type=int, default=0,
                     help="only launch the prediction kernel this many times at the final state")
     args = ap.parse_args()

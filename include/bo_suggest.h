@@ -211,7 +211,65 @@ int bo_batch_destroy(bo_batch* batch);
 int bo_batch_observe(bo_batch* batch, const int64_t* idx, const double* values, int32_t* status_out);
 /* idx_out[count]; info_out (optional) [count]. Synchronous. */
 int bo_batch_suggest(bo_batch* batch, int64_t* idx_out, int32_t* status_out, bo_suggest_info* info_out);
+/* As bo_batch_suggest for the spaces with want[i] != 0 only (others untouched, idx_out -1). */
+int bo_batch_suggest_some(bo_batch* batch, const uint8_t* want, int64_t* idx_out, int32_t* status_out,
+                          bo_suggest_info* info_out);
 int bo_batch_launch_count(const bo_batch* batch, int64_t* out);
+
+/* ---- serving: continuous batching of many sessions ----------------------- */
+/* A request loop for many concurrent tuning sessions.  A worker thread takes,
+ * in each iteration, at most one pending request of every admitted session
+ * (requests that arrived while the previous iteration ran on the GPU join
+ * this one), runs their observations as one batched update and their
+ * suggestions as one batched prediction pass, and posts completions.
+ * Sessions are admitted in arrival order while their device memory fits the
+ * budget and a slot is free, and wait in a queue otherwise (closing a
+ * session frees its memory and slot).  Each result equals what the session
+ * would get alone. */
+typedef struct bo_server bo_server;
+typedef struct bo_server_config {
+  size_t budget_bytes;       /* device memory the admitted sessions may hold       */
+  int32_t max_sessions;      /* admitted sessions at most                          */
+  int32_t pad;
+  void* stream;              /* cudaStream_t of all device work                    */
+  bo_alloc_fn alloc;         /* device memory provider of the sessions, or NULL    */
+  bo_free_fn free;
+  void* alloc_ctx;
+} bo_server_config;
+
+typedef struct bo_completion {
+  uint64_t tag;              /* the request's tag                                  */
+  int64_t session;
+  int32_t status;            /* BO_* code of the request                           */
+  int32_t observed;          /* 1 if the request's observation was applied         */
+  int64_t idx;               /* suggested valid-list index (-1 if none asked)      */
+  bo_suggest_info info;
+  double t_submit, t_start, t_done;  /* seconds, server clock                     */
+} bo_completion;
+
+typedef struct bo_server_stats {
+  int64_t admitted, queued, rejected, closed;
+  int64_t requests, completed, iterations;
+  int64_t candidates_scored;
+  int64_t bytes_in_use;
+} bo_server_stats;
+
+int bo_server_create(const bo_server_config* config, bo_server** out);
+/* Register a session (the descriptor's arrays are copied); *session_out
+ * receives its id.  BO_ERR_NOMEM if it could never fit the budget.  The
+ * descriptor's alloc / free / stream fields are ignored (the server's apply). */
+int bo_server_open(bo_server* server, const bo_space_desc* desc, int64_t* session_out);
+/* Queue a request: observe (idx, value) first if observe_idx >= 0, then
+ * suggest unless suggest == 0 (an observe-only request, e.g. to warm-start). */
+int bo_server_submit(bo_server* server, int64_t session, int64_t observe_idx, double observe_value,
+                     int32_t suggest, uint64_t tag);
+/* Up to max completions; waits up to wait_ms for the first one (0 = no wait). */
+int bo_server_poll(bo_server* server, bo_completion* out, int32_t max, int32_t* n_out, int32_t wait_ms);
+int bo_server_close(bo_server* server, int64_t session);
+int bo_server_stats_get(bo_server* server, bo_server_stats* out);
+/* Seconds on the server clock (the clock of bo_completion's times). */
+double bo_server_now(const bo_server* server);
+int bo_server_destroy(bo_server* server);
 
 /* ---- acquisition without any allocation -------------------------------- */
 /* No counterpart in the paper.  Some callers cannot allocate device memory

@@ -7,6 +7,6 @@
 `Space` wraps the C ABI of include/bo_suggest.h (libbo_suggest.so, built by
 paper_2111_14991_gb300.build).  `workloads` holds the seeded synthetic inputs.
 """
-from .bo import Batch, BOError, Space, lib  # noqa: F401
+from .bo import Batch, BOError, Server, Space, lib  # noqa: F401
 
-__all__ = ["Space", "Batch", "BOError", "lib"]
+__all__ = ["Space", "Batch", "Server", "BOError", "lib"]

@@ -65,6 +65,24 @@ class AcqParams(C.Structure):
                 ("fplus_raw", C.c_double), ("mu_s_raw", C.c_double), ("mean_var_s", C.c_double)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("max_sessions", C.c_int32), ("pad", C.c_int32),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("session", C.c_int64), ("status", C.c_int32),
+                ("observed", C.c_int32), ("idx", C.c_int64), ("info", SuggestInfo),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("admitted", C.c_int64), ("queued", C.c_int64), ("rejected", C.c_int64),
+                ("closed", C.c_int64), ("requests", C.c_int64), ("completed", C.c_int64),
+                ("iterations", C.c_int64), ("candidates_scored", C.c_int64),
+                ("bytes_in_use", C.c_int64)]
+
+
 # every symbol include/bo_suggest.h declares, with (restype, argtypes)
 SIGNATURES = {
     "bo_space_desc_init": (None, [C.POINTER(SpaceDesc)]),
@@ -82,6 +100,17 @@ SIGNATURES = {
     "bo_batch_observe": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bo_batch_suggest": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SuggestInfo)]),
     "bo_batch_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "bo_batch_suggest_some": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.POINTER(SuggestInfo)]),
+    "bo_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
+    "bo_server_open": (C.c_int, [C.c_void_p, C.POINTER(SpaceDesc), C.POINTER(C.c_int64)]),
+    "bo_server_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_int32, C.c_uint64]),
+    "bo_server_poll": (C.c_int, [C.c_void_p, C.POINTER(Completion), C.c_int32, C.POINTER(C.c_int32),
+                                 C.c_int32]),
+    "bo_server_close": (C.c_int, [C.c_void_p, C.c_int64]),
+    "bo_server_stats_get": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "bo_server_now": (C.c_double, [C.c_void_p]),
+    "bo_server_destroy": (C.c_int, [C.c_void_p]),
     "bo_get_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "bo_sync": (C.c_int, [C.c_void_p]),
     "bo_replay_enqueue": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
@@ -134,42 +163,49 @@ def _as_ptr(a, ctype):
     return a.ctypes.data_as(C.POINTER(ctype))
 
 
+def make_desc(grids, invalid_mask=None, *, nu=1.5, lengthscale=1.5, jitter=1e-10, af="ei",
+              explore="cv", lambda_const=0.01, skip_threshold=5, rif=0.1, discount=None,
+              normalize_y=True, precision="fp64", n_max=512, n_init=0, seed=0):
+    """A bo_space_desc for these arguments, and the arrays it points into."""
+    grids = [np.ascontiguousarray(g, dtype=np.float64) for g in grids]
+    d = len(grids)
+    sizes = np.array([len(g) for g in grids], dtype=np.int32)
+    vals = (C.POINTER(C.c_double) * d)(*[_as_ptr(g, C.c_double) for g in grids])
+    desc = SpaceDesc()
+    lib().bo_space_desc_init(C.byref(desc))
+    desc.d = d
+    desc.n_values = _as_ptr(sizes, C.c_int32)
+    desc.values = vals
+    mask = None
+    if invalid_mask is not None:
+        mask = np.ascontiguousarray(np.asarray(invalid_mask).reshape(-1), dtype=np.uint8)
+        desc.invalid_mask = _as_ptr(mask, C.c_uint8)
+    desc.nu, desc.lengthscale, desc.jitter = nu, lengthscale, jitter
+    desc.af = AF[af]
+    desc.explore = 0 if explore == "cv" else 1
+    desc.lambda_const = lambda_const
+    desc.skip_threshold = skip_threshold
+    desc.rif = rif
+    desc.discount = 0.0 if discount is None else discount
+    desc.y_norm = 0 if normalize_y else 1
+    desc.precision = PRECISION[precision]
+    desc.n_max = n_max
+    desc.n_init = n_init
+    desc.seed = seed
+    return desc, (grids, sizes, vals, mask)
+
+
 class Space:
     """One BO session on a discrete, normalized, constrained search space."""
 
-    def __init__(self, grids, invalid_mask=None, *, nu=1.5, lengthscale=1.5, jitter=1e-10,
-                 af="ei", explore="cv", lambda_const=0.01, skip_threshold=5, rif=0.1,
-                 discount=None, normalize_y=True, precision="fp64", n_max=512, n_init=0,
-                 seed=0, stream=None, torch_allocator=True):
+    def __init__(self, grids, invalid_mask=None, *, precision="fp64", stream=None, torch_allocator=True,
+                 **params):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the suggest library has no CPU path")
         L = lib()
-        self._grids = [np.ascontiguousarray(g, dtype=np.float64) for g in grids]
-        self.d = len(self._grids)
-        sizes = np.array([len(g) for g in self._grids], dtype=np.int32)
-        vals = (C.POINTER(C.c_double) * self.d)(*[_as_ptr(g, C.c_double) for g in self._grids])
-        desc = SpaceDesc()
-        L.bo_space_desc_init(C.byref(desc))
-        desc.d = self.d
-        desc.n_values = _as_ptr(sizes, C.c_int32)
-        desc.values = vals
-        mask = None
-        if invalid_mask is not None:
-            mask = np.ascontiguousarray(np.asarray(invalid_mask).reshape(-1), dtype=np.uint8)
-            desc.invalid_mask = _as_ptr(mask, C.c_uint8)
-        desc.nu, desc.lengthscale, desc.jitter = nu, lengthscale, jitter
-        desc.af = AF[af]
-        desc.explore = 0 if explore == "cv" else 1
-        desc.lambda_const = lambda_const
-        desc.skip_threshold = skip_threshold
-        desc.rif = rif
-        desc.discount = 0.0 if discount is None else discount
-        desc.y_norm = 0 if normalize_y else 1
-        desc.precision = PRECISION[precision]
-        desc.n_max = n_max
-        desc.n_init = n_init
-        desc.seed = seed
+        desc, self._keep = make_desc(grids, invalid_mask, precision=precision, **params)
+        self.d = desc.d
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream
@@ -307,6 +343,68 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             _check(lib().bo_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop over many sessions (native worker thread)."""
+
+    def __init__(self, budget_bytes, max_sessions=1024, stream=None, torch_allocator=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the suggest library has no CPU path")
+        cfg = ServerConfig()
+        cfg.budget_bytes = int(budget_bytes)
+        cfg.max_sessions = int(max_sessions)
+        stream = torch.cuda.current_stream() if stream is None else stream
+        self._stream = stream
+        cfg.stream = C.c_void_p(stream.cuda_stream)
+        if torch_allocator:
+            self._alloc_cbs = _torch_allocator()
+            cfg.alloc, cfg.free = self._alloc_cbs
+        h = C.c_void_p()
+        _check(lib().bo_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+
+    def open(self, grids, invalid_mask=None, **params):
+        desc, keep = make_desc(grids, invalid_mask, **params)
+        sid = C.c_int64()
+        _check(lib().bo_server_open(self._h, C.byref(desc), C.byref(sid)))
+        del keep
+        return sid.value
+
+    def submit(self, session, observe_idx=-1, observe_value=0.0, tag=0, suggest=True):
+        _check(lib().bo_server_submit(self._h, int(session), int(observe_idx), float(observe_value),
+                                      1 if suggest else 0, int(tag)))
+
+    def poll(self, max_n=1024, wait_ms=0):
+        out = (Completion * max_n)()
+        n = C.c_int32()
+        _check(lib().bo_server_poll(self._h, out, max_n, C.byref(n), int(wait_ms)))
+        return [dict(tag=c.tag, session=c.session, status=c.status, observed=bool(c.observed), idx=c.idx,
+                     info=_info_dict(c.info), t_submit=c.t_submit, t_start=c.t_start, t_done=c.t_done)
+                for c in out[:n.value]]
+
+    def close_session(self, session):
+        _check(lib().bo_server_close(self._h, int(session)))
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().bo_server_stats_get(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def now(self):
+        return lib().bo_server_now(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().bo_server_destroy(self._h))
             self._h = None
 
     def __del__(self):

@@ -59,7 +59,7 @@ def build(verbose: bool = False, force: bool = False, extra=()) -> str:
             if verbose and log.strip():
                 print(f"[{os.path.basename(src)}]\n{log}")
     if jobs or not os.path.exists(LIB):
-        cmd = [nvcc(), "-shared", ARCH, "-o", LIB] + objs + ["-lcuda"]
+        cmd = [nvcc(), "-shared", ARCH, "-o", LIB] + objs + ["-lcuda", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -265,6 +265,11 @@ int bo_batch_observe(bo_batch* b, const int64_t* idx, const double* values, int3
 }
 
 int bo_batch_suggest(bo_batch* b, int64_t* idx_out, int32_t* status_out, bo_suggest_info* info_out) {
+  return bo_batch_suggest_some(b, nullptr, idx_out, status_out, info_out);
+}
+
+int bo_batch_suggest_some(bo_batch* b, const uint8_t* want, int64_t* idx_out, int32_t* status_out,
+                          bo_suggest_info* info_out) {
   if (!b || !idx_out) return fail(BO_ERR_ARG, "null argument");
   cudaSetDevice(b->device);
   const int count = (int)b->sp.size();
@@ -278,6 +283,8 @@ int bo_batch_suggest(bo_batch* b, int64_t* idx_out, int32_t* status_out, bo_sugg
   for (int i = 0; i < count; ++i) {
     bo_space* s = b->sp[i];
     idx_out[i] = -1;
+    if (status_out) status_out[i] = BO_OK;
+    if (want && !want[i]) continue;
     if (s->poisoned) { set_status(i, fail(s->poisoned, "space %d is unusable", i)); continue; }
     bool need = false;
     int rc = suggest_begin(s, &idx_out[i], info_out ? &info_out[i] : nullptr, &need);

@@ -69,6 +69,26 @@ int bo::report_error(int code, const char* msg) {
 namespace bo {
 namespace host {
 
+size_t space_device_bytes(int d, int64_t N, int n_max, int precision, int num_sms) {
+  // the allocations of bo_space_create, each rounded up to 256 bytes
+  auto r = [](size_t b) { return (std::max<size_t>(b, 256) + 255) / 256 * 256; };
+  const int64_t N_pad = (N + kTileRows - 1) / kTileRows * kTileRows;
+  const size_t n = (size_t)((n_max + 31) / 32 * 32);
+  const size_t fsz = precision == BO_PREC_FP64 ? 8 : 4;
+  size_t t = r(d * N_pad) + r(d * 256 * 8) + r(d * 256 * 4) + r((N_pad / 32 + 1) * 4);
+  t += r(n * d * 8) + r(kXfRows * n * 4) + r(n * 8) + r(n * n * 8) + r(n * 8) + 2 * r(n * 4);
+  if (precision != BO_PREC_FP64) t += (precision == BO_PREC_TF32 ? 1 : 2) * r(lsplit_bytes((int)n, precision));
+  t += 2 * r(N_pad * fsz) + r((N_pad / 32 + num_sms) * 8) + 2 * r(n * 8) + r(8 * n * 8) + r(sizeof(DevStats));
+  t += r((size_t)4 * num_sms * 9 * sizeof(TopEntry)) + r(1024 * sizeof(bo_pass_result));
+  return t;
+}
+
+size_t space_bytes(const bo_space* s) {
+  size_t t = 0;
+  for (auto& b : s->blocks) t += b.second;
+  return t;
+}
+
 int dalloc(bo_space* s, size_t bytes, void** out) {
   bytes = std::max<size_t>(bytes, 256);
   void* p = nullptr;

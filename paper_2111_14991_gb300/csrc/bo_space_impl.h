@@ -188,6 +188,9 @@ int cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 int dalloc(bo_space* s, size_t bytes, void** out);
+// Device bytes bo_space_create allocates for these sizes, and those a space holds.
+size_t space_device_bytes(int d, int64_t N, int n_max, int precision, int num_sms);
+size_t space_bytes(const bo_space* s);
 void y_stats(const bo_space* s, double* mean, double* std_, double* ymin);
 // Scalars of a prediction pass with the given active AFs (takes the
 // contextual-variance baseline on the first pass).
