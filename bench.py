@@ -45,7 +45,12 @@ DTYPE = {"fp64": "f64", "fp16x3": "f16x3 (fp32 accumulate)", "bf16x3": "bf16x3 (
 FP64_PEAK_TFLOPS = 1.25
 # dram bytes per launch of the dominant kernel from an ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (null once the source changes)
-TRAFFIC = {}
+TRAFFIC = {
+    "predict_f64": {"bytes_per_launch": 1088256, "src_sha": "017d135c22181210", "n": 220, "N": 113247,
+                    "capture": "profiles/predict_f64_gemm7p_n220.md"},
+    "predict_tc_fp16x3": {"bytes_per_launch": 10347776 + 1280, "src_sha": "136af948615195bb", "n": 512,
+                          "N": 1032469, "capture": "profiles/predict_tc_fp16x3_gemm9p_n512.md"},
+}
 
 
 def space_for(cfg):
@@ -172,28 +177,35 @@ def tc_mma_flops(n, N):
     return 3 * 2 * 128 * 32 * cols * ((N + 127) // 128)
 
 
+def traffic_for(key, precision, n, N):
+    """Per-launch DRAM bytes from the committed ncu capture of this kernel source
+    and launch size, else None."""
+    tr = TRAFFIC.get(key)
+    if tr and tr["src_sha"] == kernel_sha(precision) and tr["n"] == n and tr["N"] == N:
+        return tr["bytes_per_launch"]
+    return None
+
+
 def roofline_for(precision, n, d, N, k1_time):
     alg = float(N) * n * (n + 1)                       # triangular contraction, flops
     if precision == "fp64":
         fl = float(flops_per_candidate(n, d)) * N
         ach = fl / k1_time / 1e12
-        tr = TRAFFIC.get("predict_f64")
         return {"bound": "alu", "kernel": "predict_f64_kernel", "achieved": round(ach, 4),
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "nominal GB300 FP64 (recipe table), not measured",
-                "traffic": tr["bytes_per_launch"] if tr and tr["src_sha"] == kernel_sha(precision) else None,
+                "peak_source": "nominal GB300 FP64 (recipe table), not measured; ncu: FP64 pipe 94.5 % busy",
+                "traffic": traffic_for("predict_f64", precision, n, N),
                 "flops_per_launch": fl, "launch_s": k1_time}
     peaks = _peaks()
     peak = peaks["bf16_tflops"] * (0.5 if precision == "tf32" else 1.0)
     ach = alg / k1_time / 1e12
     issued = (tc_mma_flops(n, N) / (3 if precision == "tf32" else 1)) / k1_time / 1e12
-    tr = TRAFFIC.get("predict_tc_" + precision)
     return {"bound": "tensor", "kernel": "predict_tc_kernel<%s>" % precision, "achieved": round(ach, 2),
             "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4),
             "peak_source": ("measured bf16 burst (MEASURED_PEAKS.json)" + (" x 1/2 nominal tf32 ratio"
                             if precision == "tf32" else "; f16 runs at the bf16 rate")),
             "mma_issued_tflops": round(issued, 1), "mma_issued_frac": round(issued / peak, 4),
-            "traffic": tr["bytes_per_launch"] if tr and tr["src_sha"] == kernel_sha(precision) else None,
+            "traffic": traffic_for("predict_tc_" + precision, precision, n, N),
             "flops_per_launch": alg, "launch_s": k1_time}
 
 
@@ -218,6 +230,7 @@ def measure_device(cfg_id, precision, steps, warm, flush, stream):
     for i, v in zip(idx[:n0], y[:n0]):
         s.observe(int(i), float(v))
     s.sync()
+    tune = s.autotune(reps=3) if precision != "fp64" else None
     times, scored, launches = [], 0, 0
     for t in range(warm + steps):
         j = n0 + t
@@ -244,7 +257,7 @@ def measure_device(cfg_id, precision, steps, warm, flush, stream):
     s.close()
     n_last = n0 + warm + steps
     return dict(sp=sp, idx=idx, y=y, n0=n0, n_last=n_last, times=times, scored=scored, launches=launches,
-                k1=statistics.median(k1), value=scored / sum(times))
+                k1=statistics.median(k1), value=scored / sum(times), tune=tune)
 
 
 def batched_workload(count, steps, warm, precision, seed=0):
@@ -277,8 +290,10 @@ def measure_batched(count, steps, warm, precision, stream):
     import torch
     sps, spaces, batch, obs = batched_workload(count, steps, warm, precision)
     hold = warm + steps
-    times, scored, flops = [], 0, 0.0
+    times, scored, flops, tune = [], 0, 0.0, None
     for t in range(warm + steps):
+        if t == warm:
+            tune = batch.autotune(reps=2)        # pipeline shapes of the batched launch
         ii = [int(i[len(i) - hold + t]) for i, _ in obs]
         yy = [float(y[len(y) - hold + t]) for _, y in obs]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -299,7 +314,7 @@ def measure_batched(count, steps, warm, precision, stream):
     for sp in spaces:
         sp.close()
     return dict(value=scored / sum(times), times=times, flops=flops, sessions=count,
-                candidates=sum(sp.n_valid for sp in sps), launches=launches)
+                candidates=sum(sp.n_valid for sp in sps), launches=launches, tune=tune)
 
 
 def measure_serving(count, rate, duration, precision, extra=160, seed=0):
@@ -443,7 +458,7 @@ def run_ours(args, rank, world):
             forms[f"config{fcfg}/{fprec}"] = {
                 "value": round(f["value"], 1), "unit": "candidates/s",
                 "ms_per_step": round(1e3 * sum(f["times"]) / len(f["times"]), 4),
-                "n_obs": f"{f['n0'] + 4}..{f['n_last']}",
+                "n_obs": f"{f['n0'] + 4}..{f['n_last']}", "autotune": f["tune"],
                 "roofline": roofline_for(fprec, f["n_last"], f["sp"].d, f["sp"].n_valid, f["k1"])}
         if not args.no_serving:
             forms["config5/fp16x3-served"] = measure_serving(args.batch_sessions, 2000.0, 4.0, "fp16x3")
@@ -455,7 +470,7 @@ def run_ours(args, rank, world):
             forms["config4/fp16x3-batched"] = {
                 "value": round(f["value"], 1), "unit": "candidates/s",
                 "ms_per_step": round(1e3 * sum(f["times"]) / len(f["times"]), 4),
-                "sessions": f["sessions"], "candidates": f["candidates"],
+                "sessions": f["sessions"], "candidates": f["candidates"], "autotune": f["tune"],
                 "what": "per step: one batched update + one batched prediction pass of every session",
                 "l2": "working set > L2 (no flush)",
                 "roofline": {"bound": "tensor", "kernel": "whole batched step", "achieved": round(ach, 2),

@@ -216,6 +216,25 @@ int bo_batch_suggest_some(bo_batch* batch, const uint8_t* want, int64_t* idx_out
                           bo_suggest_info* info_out);
 int bo_batch_launch_count(const bo_batch* batch, int64_t* out);
 
+/* ---- autotuning of the tensor-core launch --------------------------------- */
+/* Time candidate pipeline shapes of the prediction launch (depth of the K*
+ * ring, slots of the L^-1 ring, resident L^-1 pieces or not) on the space's
+ * or batch's current state, `reps` launches each with CUDA events, and keep
+ * the fastest for every later launch of the same precision, dimension bucket
+ * and padded observation count (per process).  The launches recompute the
+ * current posterior (same values).  bo_batch_autotune times the batch's last
+ * bo_batch_suggest pass (BO_ERR_STATE before one).  Reduced precision only. */
+typedef struct bo_tune_result {
+  int32_t stages_a;          /* chosen K* ring depth (0 = planner default)         */
+  int32_t b_slots;           /* chosen L^-1 ring slots                             */
+  int32_t b_resident;        /* 0 = resident pieces allowed, -1 = never            */
+  int32_t tried;             /* shapes timed                                       */
+  double best_ms;            /* median launch time of the chosen shape             */
+  double default_ms;         /* median launch time of the planner's default        */
+} bo_tune_result;
+int bo_autotune(bo_space* space, int32_t reps, bo_tune_result* out);
+int bo_batch_autotune(bo_batch* batch, int32_t reps, bo_tune_result* out);
+
 /* ---- serving: continuous batching of many sessions ----------------------- */
 /* A request loop for many concurrent tuning sessions.  A worker thread takes,
  * in each iteration, at most one pending request of every admitted session

@@ -65,6 +65,15 @@ class AcqParams(C.Structure):
                 ("fplus_raw", C.c_double), ("mu_s_raw", C.c_double), ("mean_var_s", C.c_double)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("stages_a", C.c_int32), ("b_slots", C.c_int32), ("b_resident", C.c_int32),
+                ("tried", C.c_int32), ("best_ms", C.c_double), ("default_ms", C.c_double)]
+
+
+def _tune_dict(r):
+    return {f: getattr(r, f) for f, _ in TuneResult._fields_}
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("budget_bytes", C.c_size_t), ("max_sessions", C.c_int32), ("pad", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
@@ -102,6 +111,8 @@ SIGNATURES = {
     "bo_batch_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "bo_batch_suggest_some": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.POINTER(SuggestInfo)]),
+    "bo_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(TuneResult)]),
+    "bo_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(TuneResult)]),
     "bo_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
     "bo_server_open": (C.c_int, [C.c_void_p, C.POINTER(SpaceDesc), C.POINTER(C.c_int64)]),
     "bo_server_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_int32, C.c_uint64]),
@@ -268,6 +279,11 @@ class Space:
         _check(lib().bo_last_posterior(self._h, begin, count, mu.ctypes.data, var.ctypes.data))
         return mu, var
 
+    def autotune(self, reps=3):
+        r = TuneResult()
+        _check(lib().bo_autotune(self._h, int(reps), C.byref(r)))
+        return _tune_dict(r)
+
     def predict_enqueue(self):
         _check(lib().bo_predict_enqueue(self._h))
 
@@ -339,6 +355,11 @@ class Batch:
         n = C.c_int64()
         _check(lib().bo_batch_launch_count(self._h, C.byref(n)))
         return n.value
+
+    def autotune(self, reps=3):
+        r = TuneResult()
+        _check(lib().bo_batch_autotune(self._h, int(reps), C.byref(r)))
+        return _tune_dict(r)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -39,6 +39,8 @@ struct bo_batch {
   std::vector<long long> gkey, seen_key;
   bool use_graph = true;
   int64_t launches = 0;
+  TcBatchLaunch last{};          // the last batched prediction launch (for the autotuner)
+  bool have_last = false;
 };
 
 namespace {
@@ -102,6 +104,8 @@ int enqueue_pass(bo_batch* b, int count, int n_pad_max, int nsegs, int total_blo
   L.n_pad_max = n_pad_max;
   L.nu = b->nu;
   (void)nsegs;
+  b->last = L;
+  b->have_last = true;
   if (launch_predict_tc_batch(L, b->bs) < 0) return fail(BO_ERR_CUDA, "batched prediction launch failed");
   if (launch_acquire_batch(at<AcqItem>(b->dev, b->off_acq), at<int>(b->dev, b->off_blk_item),
                            at<int>(b->dev, b->off_blk_local), at<double>(b->dev, b->off_seg_part), total_blocks,
@@ -401,6 +405,20 @@ int bo_batch_suggest_some(bo_batch* b, const uint8_t* want, int64_t* idx_out, in
     set_status(i, suggest_finish(b->sp[i], r, &idx_out[i], info_out ? &info_out[i] : nullptr));
   }
   return first_err;
+}
+
+int bo_batch_autotune(bo_batch* b, int32_t reps, bo_tune_result* out) {
+  if (!b) return fail(BO_ERR_ARG, "null batch");
+  if (b->precision == BO_PREC_FP64) return fail(BO_ERR_ARG, "the FP64 pass has no tensor-core shapes");
+  if (!b->have_last) return fail(BO_ERR_STATE, "run bo_batch_suggest once before tuning");
+  cudaSetDevice(b->device);
+  BO_CUDA(cudaStreamSynchronize(b->bs));
+  const TcBatchLaunch L = b->last;
+  const int rc = autotune_shapes(b->bs, reps, b->precision, L.dmax, L.n_pad_max, true,
+                                 [&] { return launch_predict_tc_batch(L, b->bs); }, out);
+  b->gkey.clear();               // captured graphs hold the old shape
+  b->seen_key.clear();
+  return rc;
 }
 
 int bo_batch_launch_count(const bo_batch* b, int64_t* out) {

@@ -129,6 +129,14 @@ struct TcSeg {
   int sess, tile0, tile1;
 };
 
+// Pipeline shape of a tensor-core launch (0 / -1 = the planner's default):
+// A-ring depth, B-ring slots, resident B pieces allowed (-1 = never).
+struct TcShape {
+  int stages_a = 0;
+  int b_slots = 0;
+  int b_resident = 0;
+};
+
 // A batched tensor-core launch: device arrays the host planned and uploaded.
 struct TcBatchLaunch {
   const TcSess* sess;        // [count]
@@ -180,6 +188,10 @@ int tc_dim_bucket(int d);
 int tc_plan_batch(const TcSess* sess, int count, int dmax, int grid, std::vector<TcSeg>* segs,
                   std::vector<int>* seg_begin);
 int launch_predict_tc_batch(const TcBatchLaunch& L, cudaStream_t s);
+// Autotuner hooks: launches on this thread use `shape` while it is forced
+// (nullptr ends it); a stored shape applies to every later launch of its key.
+void tc_force_shape(const TcShape* shape);
+void tc_store_shape(int precision, int dmax, int n_pad, bool batched, const TcShape& shape);
 int launch_acquire(const DevView& v, const PassArgs& a, cudaStream_t s);
 int launch_acquire(const AcqDev& v, const PassArgs& a, bool f64, cudaStream_t s);
 int acquire_grid(int64_t n_cand, int max_blocks);

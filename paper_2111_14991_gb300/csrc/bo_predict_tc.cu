@@ -21,13 +21,13 @@
 //                quarter of the chunk's observations, splits it and stores it
 //                in the K-major core-matrix layout.
 //   warps 16-19  drain the accumulator (TMEM lane = row): sum acc_k^2 q_k and
-//                acc_k b_k, write mu and var.  With n <= 256 the accumulator
+//                acc_k b_k (q, b of the space in shared memory), write mu and var.  With n <= 256 the accumulator
 //                is double-buffered, so a tile's MMAs overlap the previous
 //                tile's drain.
 //   warp 20      issues the MMAs (one thread) and owns the TMEM allocation.
 //   warp 21      streams, with bulk copies (one thread), each space's
-//                observation coordinates into shared memory (double-buffered
-//                across spaces) and the L^-1 chunks in pieces of at most 256
+//                observation coordinates and per-row factors into shared
+//                memory (double-buffered across spaces) and the L^-1 chunks in pieces of at most 256
 //                rows: a 4-slot ring, or, for one space whose pieces fit, all
 //                pieces resident, loaded once.
 // K chunk c covers observations j in [c CW, (c+1) CW); only output columns
@@ -38,6 +38,9 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "bo_internal.h"
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
       mbar_init(&acc_full[s], 1);
       mbar_init(&acc_empty[s], 4);
       mbar_init(&xs_full[s], 1);
-      mbar_init(&xs_empty[s], kProducerWarps);
+      mbar_init(&xs_empty[s], kProducerWarps + 4);   // producers and epilogue warps
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -466,10 +469,10 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     const int e = warp - kEpiWarp0;
     const int row = e * 32 + lane;
     bool ok = true;
-    int it = 0, prev = -1, seg = -1;
+    int it = 0, prev = -1, seg = -1, ks = -1;
     int n_pad = 0;
     int64_t N = 0;
-    const float* rq = nullptr;
+    const float* rq = nullptr;                   // 1/s_k^2 and beta_k/s_k of the space, shared memory
     const float* rb = nullptr;
     const uint32_t* visited = nullptr;
     float* mu = nullptr;
@@ -486,15 +489,22 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         seg = w.seg;
       }
       if (w.sess != prev) {
+        if (ks >= 0) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&xs_empty[ks % XB]);
+        }
+        ++ks;
         prev = w.sess;
         const TcSess& S = sess_of(P, w.sess);
         n_pad = S.n_pad;
         N = S.N;
-        rq = S.rowq;
-        rb = S.rowb;
+        const float* xsb = reinterpret_cast<const float*>(smem + P.off_x + (size_t)(ks % XB) * P.x_buf_bytes);
+        rq = xsb + (size_t)DMAX * n_pad;
+        rb = rq + n_pad;
         visited = S.visited;
         mu = S.mu;
         var = S.var;
+        if (!(ok = mbar_wait(&xs_full[ks % XB], (uint32_t)((ks / XB) & 1), abort_flag, status))) break;
       }
       const int as = it % P.acc_stages;
       if (!(ok = mbar_wait(&acc_full[as], (uint32_t)((it / P.acc_stages) & 1), abort_flag, status))) break;
@@ -506,8 +516,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         tmem_ld32(lane_base + (uint32_t)k0, acc);
 #pragma unroll
         for (int i = 0; i < 32; i += 4) {
-          const float4 q = __ldg(reinterpret_cast<const float4*>(rq + k0 + i));
-          const float4 b = __ldg(reinterpret_cast<const float4*>(rb + k0 + i));
+          const float4 q = *reinterpret_cast<const float4*>(rq + k0 + i);
+          const float4 b = *reinterpret_cast<const float4*>(rb + k0 + i);
           s2 = fmaf(acc[i] * acc[i], q.x, s2);
           s2 = fmaf(acc[i + 1] * acc[i + 1], q.y, s2);
           s2 = fmaf(acc[i + 2] * acc[i + 2], q.z, s2);
@@ -627,9 +637,11 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           const int xb = ks % XB;
           if (!(ok = mbar_wait(&xs_empty[xb], (uint32_t)(((ks / XB) & 1) ^ 1), abort_flag, status))) break;
           const uint32_t row_bytes = (uint32_t)(n_pad * 4);
-          mbar_arrive_tx(&xs_full[xb], row_bytes * DMAX);
+          mbar_arrive_tx(&xs_full[xb], row_bytes * (DMAX + 2));
           const uint32_t dst = xs_base + (uint32_t)(xb * P.x_buf_bytes);
           for (int p = 0; p < DMAX; ++p) bulk_g2s(dst + (uint32_t)p * row_bytes, S.xf + (size_t)p * n_max, row_bytes, &xs_full[xb]);
+          bulk_g2s(dst + (uint32_t)DMAX * row_bytes, S.rowq, row_bytes, &xs_full[xb]);
+          bulk_g2s(dst + (uint32_t)(DMAX + 1) * row_bytes, S.rowb, row_bytes, &xs_full[xb]);
           xs_issued[xb] = 1;
           xs_phase[xb] = (ks / XB) & 1;
         }
@@ -702,6 +714,18 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
 // dimension buckets: the distance loop runs over DMAX zero-padded coordinates
 int dim_bucket(int d) { return d <= 4 ? 4 : d <= 7 ? 7 : d <= 9 ? 9 : 16; }
 
+// Pipeline shapes chosen by the autotuner, per (precision, dim bucket, padded n, batched).
+std::mutex g_tune_mu;
+std::map<std::array<int, 4>, TcShape> g_tuned;
+thread_local const TcShape* g_forced = nullptr;   // a shape being timed by the autotuner
+
+TcShape shape_for(int precision, int dmax, int n_pad, bool batched) {
+  if (g_forced) return *g_forced;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find({precision, dmax, n_pad, batched ? 1 : 0});
+  return it == g_tuned.end() ? TcShape{} : it->second;
+}
+
 template <int MODE, int DMAX, bool NU52>
 int launch_mode(const TcParams& P, size_t smem, int grid, cudaStream_t s) {
   static size_t configured = 0;
@@ -744,7 +768,7 @@ int dispatch(const TcParams& P, int precision, double nu, int dmax, size_t smem,
 // most n_pad_max padded observations and dmax coordinate rows.  resident_ok:
 // the B pieces of the (single) space may stay resident.  Returns the dynamic
 // shared-memory size, 0 if nothing fits.
-size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resident_ok) {
+size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resident_ok, const TcShape& shape) {
   const int eb = precision == BO_PREC_TF32 ? 4 : 2;
   P.cw = kChunkBytes / eb;
   P.parts = precision == BO_PREC_TF32 ? 1 : 2;
@@ -754,7 +778,7 @@ size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resid
   P.tmem_cols = cols;
   P.acc_stages = 2 * cols <= 512 ? 2 : 1;
   const size_t a_stage = (size_t)P.parts * kPartBytes;
-  P.x_buf_bytes = ((size_t)dmax * n_pad_max * 4 + 127) / 128 * 128;
+  P.x_buf_bytes = ((size_t)(dmax + 2) * n_pad_max * 4 + 127) / 128 * 128;   // coordinates, 1/s^2, beta/s
   const size_t x_bytes = P.x_buf_bytes * P.xs_bufs;
   const size_t limit = 226 * 1024;   // dynamic part; the kernel's static shared memory is small
   size_t resident = 0;
@@ -762,14 +786,16 @@ size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resid
   for (int c = 0; c < n_pad_max / P.cw; ++c)
     for (int r0 = c * P.cw; r0 < n_pad_max; r0 += kPieceRows, ++pieces)
       resident += (size_t)P.parts * (std::min(kPieceRows, n_pad_max - r0) / 8) * 512;
-  P.b_resident = (resident_ok && pieces <= kMaxBSlots && resident <= (size_t)P.parts * 64 * 1024) ? 1 : 0;
-  P.b_slots = 4;
+  P.b_resident = (resident_ok && shape.b_resident >= 0 && pieces <= kMaxBSlots &&
+                  resident <= (size_t)P.parts * 64 * 1024) ? 1 : 0;
+  P.b_slots = shape.b_slots > 0 ? std::min(shape.b_slots, kMaxBSlots) : 4;
   P.b_slot_bytes = (size_t)P.parts * (kPieceRows / 8) * 512;
   const size_t b_bytes = P.b_resident ? resident : P.b_slots * P.b_slot_bytes;
   const size_t fixed = ((b_bytes + 1023) / 1024) * 1024 + ((x_bytes + 1023) / 1024) * 1024 + 512;
   if (fixed >= limit) return 0;
   int sa = (int)((limit - fixed) / a_stage);
-  sa = sa >= 8 ? 8 : sa >= 4 ? 4 : sa >= 2 ? 2 : 0;     // a power of two
+  sa = std::min(sa, 8);          // ring slots advance by counters: any depth >= 2 works
+  if (shape.stages_a > 0) sa = std::min(sa, shape.stages_a);
   if (sa < 2) return 0;
   P.stages_a = sa;
   P.off_b = (size_t)sa * a_stage;
@@ -825,7 +851,8 @@ int launch_predict_tc(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStre
   P.stats = v.stats;
   P.status = &v.stats->status;
   const int dmax = dim_bucket(v.d);
-  const size_t smem = plan_smem(P, v.precision, P.s0.n_pad, dmax, true);
+  const size_t smem = plan_smem(P, v.precision, P.s0.n_pad, dmax, true,
+                                shape_for(v.precision, dmax, P.s0.n_pad, false));
   if (!smem) return -1;
   const int grid = std::min(P.s0.num_tiles, num_sms());
   if (grid > v.max_partials) return -1;
@@ -880,11 +907,19 @@ int launch_predict_tc_batch(const TcBatchLaunch& L, cudaStream_t s) {
   P.seg_part = L.seg_part;
   P.status = L.status;
   P.xs_bufs = 2;
-  const size_t smem = plan_smem(P, L.precision, L.n_pad_max, L.dmax, false);
+  const size_t smem = plan_smem(P, L.precision, L.n_pad_max, L.dmax, false,
+                                shape_for(L.precision, L.dmax, L.n_pad_max, true));
   if (!smem) return -1;
   return dispatch(P, L.precision, L.nu, L.dmax, smem, L.grid, s);
 }
 
 int tc_dim_bucket(int d) { return dim_bucket(d); }
+
+void tc_force_shape(const TcShape* shape) { g_forced = shape; }
+
+void tc_store_shape(int precision, int dmax, int n_pad, bool batched, const TcShape& shape) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[{precision, dmax, n_pad, batched ? 1 : 0}] = shape;
+}
 
 }  // namespace bo

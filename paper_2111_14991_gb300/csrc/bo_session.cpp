@@ -588,6 +588,17 @@ int bo_predict_enqueue(bo_space* s) {
   return BO_OK;
 }
 
+int bo_autotune(bo_space* s, int32_t reps, bo_tune_result* out) {
+  if (!s) return fail(BO_ERR_ARG, "null space");
+  if (s->desc.precision == BO_PREC_FP64) return fail(BO_ERR_ARG, "the FP64 pass has no tensor-core shapes");
+  if (s->n_fit == 0) return fail(BO_ERR_STATE, "no valid observation to predict from");
+  cudaSetDevice(s->device);
+  BO_CUDA(cudaStreamSynchronize(s->stream));
+  const TcSess ts = tc_session(s->v, s->n_fit);
+  return autotune_shapes(s->stream, reps, s->desc.precision, tc_dim_bucket(s->d), ts.n_pad, false,
+                         [&] { return launch_predict_tc(s->v, s->n_fit, s->N - s->n_visited, s->stream); }, out);
+}
+
 int bo_get_factor(bo_space* s, double* linv_out, double* beta_out, int32_t* n_out) {
   if (!s) return fail(BO_ERR_ARG, "null space");
   cudaSetDevice(s->device);

@@ -205,5 +205,79 @@ int suggest_begin(bo_space* s, int64_t* idx_out, bo_suggest_info* info, bool* ne
 // Finish a round from the pass result r: picks, queue, the first pick.
 int suggest_finish(bo_space* s, const bo_pass_result& r, int64_t* idx_out, bo_suggest_info* info);
 
+// Time `launch` (a function enqueueing one prediction launch on `stream`,
+// returning < 0 on failure) under each candidate TcShape; store and report the
+// fastest under `key`.
+template <typename Launch>
+int autotune_shapes(cudaStream_t stream, int reps, int precision, int dmax, int n_pad, bool batched,
+                    Launch launch, bo_tune_result* out);
+
+}  // namespace host
+}  // namespace bo
+
+namespace bo {
+namespace host {
+
+template <typename Launch>
+int autotune_shapes(cudaStream_t stream, int reps, int precision, int dmax, int n_pad, bool batched,
+                    Launch launch, bo_tune_result* out) {
+  reps = std::max(1, std::min(reps, 50));
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(BO_ERR_CUDA, "event creation failed");
+  auto time_shape = [&](const TcShape& shape, double* ms) -> bool {
+    tc_force_shape(&shape);
+    bool ok = launch() >= 0;                      // warm (and function attributes)
+    std::vector<float> t;
+    for (int r = 0; ok && r < reps; ++r) {
+      cudaEventRecord(e0, stream);
+      ok = launch() >= 0;
+      cudaEventRecord(e1, stream);
+      float x = 0.0f;
+      ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&x, e0, e1) == cudaSuccess;
+      t.push_back(x);
+    }
+    tc_force_shape(nullptr);
+    if (!ok || t.empty()) return false;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return true;
+  };
+  TcShape best{};
+  double best_ms = 0.0, default_ms = 0.0;
+  int tried = 0;
+  if (!time_shape(TcShape{}, &default_ms)) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return fail(BO_ERR_CUDA, "the default prediction launch failed");
+  }
+  best_ms = default_ms;
+  ++tried;
+  for (int sa : {2, 3, 4, 6, 8})
+    for (int bs : {2, 3, 4, 6})
+      for (int res : {0, -1}) {
+        TcShape sh;
+        sh.stages_a = sa;
+        sh.b_slots = bs;
+        sh.b_resident = res;
+        double ms = 0.0;
+        if (!time_shape(sh, &ms)) continue;   // does not fit shared memory
+        ++tried;
+        if (ms < best_ms) { best_ms = ms; best = sh; }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tc_store_shape(precision, dmax, n_pad, batched, best);
+  if (out) {
+    out->stages_a = best.stages_a;
+    out->b_slots = best.b_slots;
+    out->b_resident = best.b_resident;
+    out->tried = tried;
+    out->best_ms = best_ms;
+    out->default_ms = default_ms;
+  }
+  return BO_OK;
+}
+
 }  // namespace host
 }  // namespace bo

@@ -168,3 +168,15 @@ def test_replay_matches_suggest():
         assert r["top_mu"][0][0] == pytest.approx(mu[i0], abs=1e-6)
     a.close()
     b.close()
+
+
+def test_autotune_keeps_results():
+    """The autotuner only changes pipeline depths: the posterior is bit-identical."""
+    sp = W.config2_space()
+    g, idx, y = state(sp, 150, 4, "fp16x3", n_max=160)
+    mu0, var0 = g.predict()
+    r = g.autotune(reps=2)
+    assert r["tried"] > 1 and r["best_ms"] <= r["default_ms"] + 1e-9
+    mu1, var1 = g.predict()
+    assert np.array_equal(mu0, mu1) and np.array_equal(var0, var1)
+    g.close()
