@@ -18,12 +18,17 @@
 // CTA organisation (persistent, one CTA per SM, 128 candidates per tile):
 //   warps 0-15   produce K* chunks: thread (row = t % 128, quarter = t / 128)
 //                evaluates the Matern covariance of its candidate against a
-//                quarter of the chunk's observations, splits it and stores it
-//                in the K-major core-matrix layout.
+//                quarter of the chunk's observations (packed f32x2, over the
+//                space's own d coordinates), splits it and stores it in the
+//                K-major core-matrix layout.  The next tile's candidate codes
+//                are fetched while the current tile is computed.
 //   warps 16-19  drain the accumulator (TMEM lane = row): sum acc_k^2 q_k and
-//                acc_k b_k (q, b of the space in shared memory), write mu and var.  With n <= 256 the accumulator
-//                is double-buffered, so a tile's MMAs overlap the previous
-//                tile's drain.
+//                acc_k b_k (q, b of the space in shared memory), write mu and
+//                var.  Column block c is final once chunk c's MMAs complete,
+//                so it is drained then (one barrier per block), and each
+//                256-column region is handed back after its last block: the
+//                next tile's first MMAs into a region wait only for that
+//                region.  With n <= 256 the accumulator is double-buffered.
 //   warp 20      issues the MMAs (one thread) and owns the TMEM allocation.
 //   warp 21      streams, with bulk copies (one thread), each space's
 //                observation coordinates and per-row factors into shared
@@ -59,6 +64,7 @@ constexpr int kPartBytes = kRows * kChunkBytes;   // one split part of an A stag
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 constexpr int kPieceRows = 256;         // rows of L^-1 per B piece (= max MMA N)
 constexpr int kMaxBSlots = 16;
+constexpr int kAccBars = 32;            // per accumulator column block: 2 buffers x 16, or 1 x 32
 
 struct TcParams {
   TcSess s0;                 // the space, when batch == 0
@@ -233,6 +239,19 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* r) {
+  uint32_t u[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+        "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+        "=r"(u[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(u[i]);
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* r) {
   uint32_t u[32];
   asm volatile(
@@ -278,22 +297,65 @@ __device__ __forceinline__ void lds2x64(uint32_t addr, uint64_t& a, uint64_t& b)
   asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
 }
 
-// Matern covariance in FP32 from u^2, the squared distance in units where
-// u = t log2(e), t = sqrt(2 nu) r / l (the coordinate tables carry the scale):
-// u from the hardware reciprocal square root and one Newton step, e^-t = 2^-u
-// from the hardware exp2, then (1 + t) e^-t or (1 + t + t^2/3) e^-t.
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t dup2(float x) { return pk2(x, x); }
+
+// Matern covariance in FP32 for two squared distances at once (one packed
+// word), in units where u = t log2(e), t = sqrt(2 nu) r / l (the coordinate
+// tables carry the scale; the accumulators start at 1e-30 so u^2 > 0):
+// u from the hardware reciprocal square root and one Newton step on the
+// residual u0^2 - u^2, e^-t = 2^-u from the hardware exp2, then (1 + t) e^-t
+// or (1 + t + t^2/3) e^-t.  Everything but the four MUFU operations runs on
+// the packed f32x2 pipe.
 template <bool NU52>
-__device__ __forceinline__ float matern_u2(float u2) {
-  u2 = fmaxf(u2, 1e-30f);
-  const float rs = rsqrtf(u2);
-  float u = u2 * rs;
-  u = fmaf(fmaf(-u, u, u2), 0.5f * rs, u);
-  const float e = ex2_approx(-u);
-  const float t = u * 0.6931471805599453f;
+__device__ __forceinline__ uint64_t matern2(uint64_t u2p) {
+  float a, b;
+  upk2(u2p, a, b);
+  const uint64_t rs = pk2(rsqrtf(a), rsqrtf(b));
+  const uint64_t u0 = mul2(u2p, rs);
+  const uint64_t nu2 = mul2(u2p, dup2(-1.0f));
+  const uint64_t hn = mul2(rs, dup2(-0.5f));
+  const uint64_t u = fma2(fma2(u0, u0, nu2), hn, u0);
+  float ua, ub;
+  upk2(u, ua, ub);
+  const uint64_t e = pk2(ex2_approx(-ua), ex2_approx(-ub));
+  const uint64_t t = mul2(u, dup2(0.6931471805599453f));
   if constexpr (NU52)
-    return fmaf(t * e, fmaf(t, 1.0f / 3.0f, 1.0f), e);
+    return fma2(mul2(t, e), fma2(t, dup2(1.0f / 3.0f), dup2(1.0f)), e);
   else
-    return fmaf(t, e, e);
+    return fma2(t, e, e);
+}
+
+// Squared scaled distances of one candidate (xcp: its coordinates, twice per
+// word) to this thread's observations of a chunk (coordinates rows in shared
+// memory at xrow, n_pad floats apart), two observations per packed
+// instruction; accumulators start at 1e-30 so that u^2 > 0.  CHECK: the
+// space has fewer than DMAX coordinates (d, warp-uniform).
+template <int MODE, int DMAX, bool CHECK>
+__device__ __forceinline__ void sq_dist(const uint64_t* xcp, uint32_t xrow, int n_pad, int d, uint64_t* r2p) {
+  const uint64_t eps = dup2(1e-30f);
+  r2p[0] = r2p[1] = r2p[2] = r2p[3] = eps;
+#pragma unroll
+  for (int p = 0; p < DMAX; ++p) {
+    if (CHECK && p >= d) break;
+    uint64_t o0, o1;
+    lds2x64(xrow + (uint32_t)(p * n_pad * 4), o0, o1);
+    uint64_t df = sub2(xcp[p], o0);
+    r2p[0] = fma2(df, df, r2p[0]);
+    df = sub2(xcp[p], o1);
+    r2p[1] = fma2(df, df, r2p[1]);
+    if constexpr (MODE != BO_PREC_TF32) {
+      lds2x64(xrow + (uint32_t)(p * n_pad * 4 + 16), o0, o1);
+      df = sub2(xcp[p], o0);
+      r2p[2] = fma2(df, df, r2p[2]);
+      df = sub2(xcp[p], o1);
+      r2p[3] = fma2(df, df, r2p[3]);
+    }
+  }
 }
 
 // pack two values of the split parts: hi and lo 16-bit words, or one tf32 word
@@ -329,7 +391,8 @@ template <int MODE, int DMAX, bool NU52>
 __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_constant__ TcParams P) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cw = P.cw, parts = P.parts, SA = P.stages_a, XB = P.xs_bufs;
+  constexpr int CW = MODE == BO_PREC_TF32 ? 16 : 32;   // observations per K chunk
+  const int cw = CW, parts = P.parts, SA = P.stages_a, XB = P.xs_bufs;
   uint8_t* sa = smem;                                   // [SA][parts][8 KB]
   uint8_t* sb = smem + P.off_b;                         // B slots or resident pieces
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P.off_bar);
@@ -337,12 +400,14 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
   uint64_t* a_empty = bars + SA;
   uint64_t* b_full = bars + 2 * SA;                            // [kMaxBSlots]
   uint64_t* b_empty = bars + 2 * SA + kMaxBSlots;              // [kMaxBSlots]
-  uint64_t* acc_full = bars + 2 * SA + 2 * kMaxBSlots;         // [2]
-  uint64_t* acc_empty = bars + 2 * SA + 2 * kMaxBSlots + 2;    // [2]
-  uint64_t* xs_full = bars + 2 * SA + 2 * kMaxBSlots + 4;      // [2]
-  uint64_t* xs_empty = bars + 2 * SA + 2 * kMaxBSlots + 6;     // [2]
-  uint64_t* drain = bars + 2 * SA + 2 * kMaxBSlots + 8;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SA + 2 * kMaxBSlots + 9);
+  // acc_full[16 buffer + block]: one barrier per accumulator column block, so
+  // that the MMA issuer is never more than one phase ahead of the epilogue on any
+  uint64_t* acc_full = bars + 2 * SA + 2 * kMaxBSlots;                     // [kAccBars]
+  uint64_t* acc_empty = bars + 2 * SA + 2 * kMaxBSlots + kAccBars;         // [2] regions
+  uint64_t* xs_full = bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 2;       // [2]
+  uint64_t* xs_empty = bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 4;      // [2]
+  uint64_t* drain = bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 6;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 7);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ double red[4];   // per epilogue warp
   __shared__ bool s_last;
@@ -352,8 +417,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
   if (threadIdx.x == 0) {
     for (int s = 0; s < SA; ++s) { mbar_init(&a_full[s], kProducerWarps); mbar_init(&a_empty[s], 1); }
     for (int s = 0; s < kMaxBSlots; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
+    for (int s = 0; s < kAccBars; ++s) mbar_init(&acc_full[s], 1);
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&acc_full[s], 1);
       mbar_init(&acc_empty[s], 4);
       mbar_init(&xs_full[s], 1);
       mbar_init(&xs_empty[s], kProducerWarps + 4);   // producers and epilogue warps
@@ -389,6 +454,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     const uint8_t* codes = nullptr;
     const float* vt = nullptr;
     uint32_t xs = xs_base;
+    uint32_t code_next[DMAX];
+    bool have_next = false;
     Work w;
     for (bool more = work_begin(P, w); more && ok; more = work_next(P, w)) {
       if (w.sess != prev) {                      // next space: its coordinates, once copied in
@@ -408,53 +475,56 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         xs = xs_base + (uint32_t)((ks % XB) * P.x_buf_bytes);
         if (!(ok = mbar_wait(&xs_full[ks % XB], (uint32_t)((ks / XB) & 1), abort_flag, status))) break;
       }
+      // this tile's candidate codes: prefetched during the previous tile, except for the first
       const int64_t cand = (int64_t)w.tile * kRows + row;
+      uint32_t cc[DMAX];
+#pragma unroll
+      for (int p = 0; p < DMAX; ++p)
+        cc[p] = have_next ? code_next[p] : (p < d ? (uint32_t)codes[(int64_t)p * N_pad + cand] : 0u);
+      {
+        Work wn = w;
+        have_next = work_next(P, wn);
+        if (have_next) {
+          const TcSess& Sn = sess_of(P, wn.sess);
+          const int64_t cn = (int64_t)wn.tile * kRows + row;
+          const int dn = Sn.d;
+          const int64_t Nn = Sn.N_pad;
+          const uint8_t* cp = Sn.codes;
+#pragma unroll
+          for (int p = 0; p < DMAX; ++p) code_next[p] = p < dn ? (uint32_t)cp[(int64_t)p * Nn + cn] : 0u;
+        }
+      }
       uint64_t xcp[DMAX];                      // candidate coordinate, twice per word
 #pragma unroll
-      for (int p = 0; p < DMAX; ++p) {
-        const float x = p < d ? vt[p * 256 + codes[(int64_t)p * N_pad + cand]] : 0.0f;
-        xcp[p] = pk2(x, x);
-      }
+      for (int p = 0; p < DMAX; ++p) xcp[p] = dup2(p < d ? vt[p * 256 + cc[p]] : 0.0f);
       for (int c = 0; c < chunks && ok; ++c) {
         const int j0 = c * cw + quarter * jq;
-        // K* for this thread's observations, computed before waiting for the ring slot:
-        // squared distances two observations per packed instruction
-        uint64_t r2p[4] = {0ull, 0ull, 0ull, 0ull};
+        // K* for this thread's observations, computed before waiting for the ring slot
+        uint64_t r2p[4];
         const uint32_t xrow = xs + (uint32_t)(j0 * 4);
+        if (d == DMAX)
+          sq_dist<MODE, DMAX, false>(xcp, xrow, n_pad, d, r2p);
+        else
+          sq_dist<MODE, DMAX, true>(xcp, xrow, n_pad, d, r2p);
+        uint64_t kv[4];
 #pragma unroll
-        for (int p = 0; p < DMAX; ++p) {
-          uint64_t o0, o1;
-          lds2x64(xrow + (uint32_t)(p * n_pad * 4), o0, o1);
-          uint64_t df = sub2(xcp[p], o0);
-          r2p[0] = fma2(df, df, r2p[0]);
-          df = sub2(xcp[p], o1);
-          r2p[1] = fma2(df, df, r2p[1]);
-          if constexpr (MODE != BO_PREC_TF32) {
-            lds2x64(xrow + (uint32_t)(p * n_pad * 4 + 16), o0, o1);
-            df = sub2(xcp[p], o0);
-            r2p[2] = fma2(df, df, r2p[2]);
-            df = sub2(xcp[p], o1);
-            r2p[3] = fma2(df, df, r2p[3]);
-          }
-        }
-        float kv[8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (2 * q < jq) {
-            float a, b;
-            upk2(r2p[q], a, b);
-            kv[2 * q] = matern_u2<NU52>(a);
-            kv[2 * q + 1] = matern_u2<NU52>(b);
-          }
-        }
+        for (int q = 0; q < 4; ++q)
+          if (2 * q < jq) kv[q] = matern2<NU52>(r2p[q]);
         if (!(ok = mbar_wait(&a_empty[s], ph ^ 1, abort_flag, status))) break;
         const uint32_t stage = a_base + (uint32_t)(s * parts * kPartBytes) + row_off;
         if constexpr (MODE == BO_PREC_TF32) {
-          st_shared_v4(stage, to_tf32(kv[0]), to_tf32(kv[1]), to_tf32(kv[2]), to_tf32(kv[3]));
+          float k0, k1, k2, k3;
+          upk2(kv[0], k0, k1);
+          upk2(kv[1], k2, k3);
+          st_shared_v4(stage, to_tf32(k0), to_tf32(k1), to_tf32(k2), to_tf32(k3));
         } else {
           uint32_t h[4], l[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) split2<MODE>(kv[2 * q], kv[2 * q + 1], h[q], l[q]);
+          for (int q = 0; q < 4; ++q) {
+            float ka, kb;
+            upk2(kv[q], ka, kb);
+            split2<MODE>(ka, kb, h[q], l[q]);
+          }
           st_shared_v4(stage, h[0], h[1], h[2], h[3]);
           st_shared_v4(stage + kPartBytes, l[0], l[1], l[2], l[3]);
         }
@@ -470,7 +540,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     const int row = e * 32 + lane;
     bool ok = true;
     int it = 0, prev = -1, seg = -1, ks = -1;
-    int n_pad = 0;
+    int n_pad = 0, chunks = 0;
+    uint32_t par[2] = {0u, 0u};                  // phase parity of each block barrier, per buffer
     int64_t N = 0;
     const float* rq = nullptr;                   // 1/s_k^2 and beta_k/s_k of the space, shared memory
     const float* rb = nullptr;
@@ -497,6 +568,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         prev = w.sess;
         const TcSess& S = sess_of(P, w.sess);
         n_pad = S.n_pad;
+        chunks = S.chunks;
         N = S.N;
         const float* xsb = reinterpret_cast<const float*>(smem + P.off_x + (size_t)(ks % XB) * P.x_buf_bytes);
         rq = xsb + (size_t)DMAX * n_pad;
@@ -506,31 +578,44 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         var = S.var;
         if (!(ok = mbar_wait(&xs_full[ks % XB], (uint32_t)((ks / XB) & 1), abort_flag, status))) break;
       }
+      // column block c (the chunk's CW columns) is final once chunk c's MMAs
+      // complete: drain it then, and release each 256-column region of the
+      // buffer after its last block
       const int as = it % P.acc_stages;
-      if (!(ok = mbar_wait(&acc_full[as], (uint32_t)((it / P.acc_stages) & 1), abort_flag, status))) break;
-      tc_fence_after();
-      float s2 = 0.0f, sm = 0.0f;
       const uint32_t lane_base = tmem + (uint32_t)(as * P.tmem_cols) + ((uint32_t)(e * 32) << 16);
-      for (int k0 = 0; k0 < n_pad; k0 += 32) {
+      uint64_t s2p = 0ull, smp = 0ull;           // two columns per packed word
+      for (int c = 0; c < chunks && ok; ++c) {
+        if (!(ok = mbar_wait(&acc_full[as * 16 + c], (par[as] >> c) & 1u, abort_flag, status))) break;
+        par[as] ^= 1u << c;
+        tc_fence_after();
+        const int k0 = c * CW;
         float acc[32];
-        tmem_ld32(lane_base + (uint32_t)k0, acc);
+        if constexpr (CW == 16)
+          tmem_ld16(lane_base + (uint32_t)k0, acc);
+        else
+          tmem_ld32(lane_base + (uint32_t)k0, acc);
 #pragma unroll
-        for (int i = 0; i < 32; i += 4) {
+        for (int i = 0; i < CW; i += 4) {
           const float4 q = *reinterpret_cast<const float4*>(rq + k0 + i);
           const float4 b = *reinterpret_cast<const float4*>(rb + k0 + i);
-          s2 = fmaf(acc[i] * acc[i], q.x, s2);
-          s2 = fmaf(acc[i + 1] * acc[i + 1], q.y, s2);
-          s2 = fmaf(acc[i + 2] * acc[i + 2], q.z, s2);
-          s2 = fmaf(acc[i + 3] * acc[i + 3], q.w, s2);
-          sm = fmaf(acc[i], b.x, sm);
-          sm = fmaf(acc[i + 1], b.y, sm);
-          sm = fmaf(acc[i + 2], b.z, sm);
-          sm = fmaf(acc[i + 3], b.w, sm);
+          const uint64_t a01 = pk2(acc[i], acc[i + 1]), a23 = pk2(acc[i + 2], acc[i + 3]);
+          s2p = fma2(mul2(a01, pk2(q.x, q.y)), a01, s2p);
+          s2p = fma2(mul2(a23, pk2(q.z, q.w)), a23, s2p);
+          smp = fma2(a01, pk2(b.x, b.y), smp);
+          smp = fma2(a23, pk2(b.z, b.w), smp);
+        }
+        const int kend = k0 + CW;
+        if (kend == n_pad || (kend & (kPieceRows - 1)) == 0) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[as + ((kend - 1) >> 8)]);
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[as]);
+      if (!ok) break;
+      float s2a, s2b, sma, smb;
+      upk2(s2p, s2a, s2b);
+      upk2(smp, sma, smb);
+      const float s2 = s2a + s2b, sm = sma + smb;
       const int64_t cand = (int64_t)w.tile * kRows + row;
       const float vr = fmaxf(0.0f, 1.0f - s2);
       mu[cand] = sm;
@@ -551,6 +636,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
       bool ok = true, issued = false;
       int it = 0, sa_i = 0, tb = 0, prev = -1, n_pad = 0, chunks = 0;
       uint32_t pha = 0, phb = 0;
+      uint32_t fill[2] = {0u, 0u};  // tiles started per accumulator region
       Work w;
       for (bool more = work_begin(P, w); more && ok; more = work_next(P, w), ++it) {
         if (w.sess != prev) {
@@ -560,9 +646,6 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           chunks = S.chunks;
         }
         const int as = it % P.acc_stages;
-        if (!(ok = mbar_wait(&acc_empty[as], (uint32_t)(((it / P.acc_stages) & 1) ^ 1), abort_flag, status)))
-          break;
-        tc_fence_after();
         const uint32_t d_base = tmem + (uint32_t)(as * P.tmem_cols);
         int q = 0;                  // piece index within the tile
         uint32_t packed = 0;        // resident byte offset of piece q
@@ -570,25 +653,37 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           const int s = sa_i;
           if (!(ok = mbar_wait(&a_full[s], pha, abort_flag, status))) break;
           tc_fence_after();
-          const uint32_t a_st = a_base + (uint32_t)(s * parts * kPartBytes);
+          const uint64_t ad0 = smem_desc(a_base + (uint32_t)(s * parts * kPartBytes), 128, 512);
           for (int r0 = c * cw; r0 < n_pad && ok; r0 += kPieceRows, ++q) {
             const int wd = min(kPieceRows, n_pad - r0);         // rows of this piece = MMA N
             const uint32_t part_bytes = (uint32_t)((wd >> 3) * 512);
+            if (c == 0) {             // first write to this 256-column region since its last drain
+              const int r = as + (r0 >> 8);
+              if (!(ok = mbar_wait(&acc_empty[r], (fill[r] & 1u) ^ 1u, abort_flag, status))) break;
+              ++fill[r];
+              tc_fence_after();
+            }
             const int slot = P.b_resident ? q : tb;
             if (!(ok = mbar_wait(&b_full[slot], P.b_resident ? 0u : phb, abort_flag, status))) break;
             tc_fence_after();
             const uint32_t b_st = b_base + (P.b_resident ? packed : (uint32_t)(tb * P.b_slot_bytes));
-            const int nsplit = parts == 2 ? 3 : 1;
-            for (int sp = 0; sp < nsplit; ++sp) {
+            // descriptors advance by address >> 4: +16 is the next 16-element K step
+            const uint64_t bd0 = smem_desc(b_st, 128, 512);
+            const uint32_t idesc = instr_desc(fmt, kRows, wd);
+            const uint32_t dcol = d_base + (uint32_t)r0;
+            const uint32_t first = c > 0 ? 1u : 0u;
+            if (parts == 2) {
               // products (hi, lo), (lo, hi), (hi, hi): small terms first
-              const int pa = parts == 2 ? (sp == 1 ? 1 : 0) : 0;
-              const int pb = parts == 2 ? (sp == 0 ? 1 : 0) : 0;
-              for (int kk = 0; kk < 2; ++kk) {
-                const uint64_t ad = smem_desc(a_st + (uint32_t)(pa * kPartBytes + kk * 256), 128, 512);
-                const uint64_t bd = smem_desc(b_st + (uint32_t)(pb * part_bytes + kk * 256), 128, 512);
-                const uint32_t acc = (c > 0 || sp > 0 || kk > 0) ? 1u : 0u;
-                mma<MODE>(d_base + (uint32_t)r0, ad, bd, instr_desc(fmt, kRows, wd), acc);
-              }
+              const uint64_t pbo = (uint64_t)(part_bytes >> 4), pao = (uint64_t)(kPartBytes >> 4);
+              mma<MODE>(dcol, ad0, bd0 + pbo, idesc, first);
+              mma<MODE>(dcol, ad0 + 16, bd0 + pbo + 16, idesc, 1u);
+              mma<MODE>(dcol, ad0 + pao, bd0, idesc, 1u);
+              mma<MODE>(dcol, ad0 + pao + 16, bd0 + 16, idesc, 1u);
+              mma<MODE>(dcol, ad0, bd0, idesc, 1u);
+              mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
+            } else {
+              mma<MODE>(dcol, ad0, bd0, idesc, first);
+              mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
             }
             issued = true;
             packed += part_bytes * (uint32_t)parts;
@@ -599,9 +694,9 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           }
           if (!ok) break;
           mma_commit(&a_empty[s]);
+          mma_commit(&acc_full[as * 16 + c]);  // column block c of this buffer is final
           if (++sa_i == SA) { sa_i = 0; pha ^= 1; }
         }
-        if (ok) mma_commit(&acc_full[as]);
       }
       if (issued) {   // every MMA of this CTA has completed before TMEM is released
         mma_commit(drain);
@@ -801,7 +896,7 @@ size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resid
   P.off_b = (size_t)sa * a_stage;
   P.off_x = P.off_b + ((b_bytes + 1023) / 1024) * 1024;
   P.off_bar = (P.off_x + x_bytes + 15) / 16 * 16;
-  const size_t smem = P.off_bar + (size_t)(2 * sa + 2 * kMaxBSlots + 10) * 8 + 16;
+  const size_t smem = P.off_bar + (size_t)(2 * sa + 2 * kMaxBSlots + kAccBars + 8) * 8 + 16;
   // every descriptor footprint stays inside its stage: A parts are 128 rows x
   // 64 B; a B piece [r0, r0 + w) ends at the end of its part
   if ((size_t)15 * 512 + 256 + 255 >= (size_t)kPartBytes) return 0;
