@@ -65,6 +65,18 @@ enum {
   BO_PREC_TF32 = 3     /* tcgen05 tf32, 1 product, FP32 accumulate                 */
 };
 
+/* initial sample (Sec. III-E; Table I selects maximin):
+ *   RANDOM   uniform random valid configurations
+ *   LHS      a Latin hypercube over the parameters' value lists: parameter p
+ *            of sample i takes value floor(u m_p) of its m_p values, with
+ *            u = (pi_p(i) + U) / n_init, pi_p a random permutation of the
+ *            n_init strata and U uniform in [0, 1); restricted or repeated
+ *            configurations are replaced by random valid ones
+ *   MAXIMIN  as LHS, keeping of init_designs Latin hypercubes the one whose
+ *            smallest pairwise distance between normalized points is largest
+ * The exact draw order is given at bo_initial_design. */
+enum { BO_INIT_RANDOM = 0, BO_INIT_LHS = 1, BO_INIT_MAXIMIN = 2 };
+
 #define BO_MAX_PARAMS 16   /* parameters per space                             */
 #define BO_MAX_VALUES 256  /* values per parameter (codes are uint8)          */
 #define BO_MAX_OBS 512     /* largest n_max (valid observations fitted)        */
@@ -93,9 +105,11 @@ typedef struct bo_space_desc {
   int32_t y_norm;                 /* BO_YNORM_*                                      */
   int32_t precision;              /* BO_PREC_*                                       */
   int32_t n_max;                  /* capacity in valid observations, 1..BO_MAX_OBS   */
-  int32_t n_init;                 /* suggests drawn at random while fewer
-                                     observations than this exist                    */
-  uint64_t seed;                  /* splitmix64 seed of those random draws           */
+  int32_t n_init;                 /* initial-sample suggests are made while fewer
+                                     valid (finite) observations than this exist     */
+  uint64_t seed;                  /* splitmix64 seed of every random draw            */
+  int32_t init_mode;              /* BO_INIT_*: how the initial sample is drawn      */
+  int32_t init_designs;           /* BO_INIT_MAXIMIN: Latin hypercube designs compared */
   bo_alloc_fn alloc;              /* device memory provider, or NULL                 */
   bo_free_fn free;
   void* alloc_ctx;
@@ -104,8 +118,32 @@ typedef struct bo_space_desc {
 
 /* Fill `desc` with the defaults of Table I: nu = 3/2, l = 1.5 with the
  * contextual-variance factor, jitter 1e-10, EI, skip threshold 5,
- * rif 0.1, Table I discounts, standardized y, FP64, n_max = 512. */
+ * rif 0.1, Table I discounts, standardized y, FP64, n_max = 512, maximin
+ * initial sampling over 100 designs (n_init = 0: the caller supplies it). */
 void bo_space_desc_init(bo_space_desc* desc);
+
+/* The initial sample a space built from `desc` draws (Sec. III-E), computed
+ * on the host from desc->d, n_values, values, invalid_mask, init_mode,
+ * init_designs and seed alone (no device, no space needed).  idx_out[count]
+ * receives distinct valid-list indices; count must be in [1, number of valid
+ * configurations].  Draws come from one splitmix64 stream seeded with
+ * desc->seed, in this order:
+ *   RANDOM: per sample, r = next() mod N_valid, redrawn while already taken.
+ *   LHS / MAXIMIN, per design (one design for LHS, init_designs for MAXIMIN),
+ *     per parameter p in order: a Fisher-Yates shuffle of the strata
+ *     0..count-1 (for i = count-1 down to 1: swap i with next() mod (i+1)),
+ *     then per sample i the jitter U = (next() >> 11) / 2^53; the value index
+ *     floor((pi_p(i) + U) m_p / count) is computed exactly in integers.
+ *     MAXIMIN keeps the first design with the largest minimum over pairs of
+ *     sum_p (x_ip - x_jp)^2 (FP64, p in order, no fused multiply-add).
+ *     The kept design's samples map to configurations in order; a restricted
+ *     one, or a repeat of an earlier sample, is replaced (again in order) by
+ *     r = next() mod N_valid, redrawn while already taken.
+ * A space with n_init > 0 and init_mode LHS / MAXIMIN suggests exactly this
+ * design (count = min(n_init, N_valid)) first, skipping configurations
+ * already observed, then random unobserved ones until n_init valid
+ * observations exist.  Errors: BO_ERR_ARG. */
+int bo_initial_design(const bo_space_desc* desc, int32_t count, int64_t* idx_out);
 
 typedef struct bo_space bo_space;   /* opaque, owned by the library */
 

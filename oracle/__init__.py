@@ -17,6 +17,10 @@ Parity status of each part (what pins it, see tests/test_oracle_*.py):
   contextual λ      pinned: exact ratio at the first pass, linearity
   argmax / top-k    pinned: brute force
   dos               pinned: hand sums
+  initial sample    pinned: Latin property (one value / stratum per parameter),
+                    brute-force 2x2 designs, maximin monotone in the number of
+                    designs and above its first design, restricted samples
+                    replaced with the valid ones kept in place
   multi / adv-multi selection
                     parity unpinned against the paper (it prints no trace);
                     pinned only to the readings of Sec. III-G listed in the
@@ -24,4 +28,5 @@ Parity status of each part (what pins it, see tests/test_oracle_*.py):
 """
 from .bo_oracle import *  # noqa: F401,F403
 from .selection import *  # noqa: F401,F403
+from .sampling import *  # noqa: F401,F403
 from .session import *  # noqa: F401,F403

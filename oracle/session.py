@@ -14,10 +14,14 @@ Readings (the paper is silent on these):
     mu_s = mean of the valid raw observations made before it, and
     mean_var_s = that pass's mean variance, so lambda = f+/mu_s there.  The
     mean variance is over the valid, non-evaluated configurations scored.
-  * Initial sampling handled by the session (n_init > 0) and suggests made
-    with no valid observation yet draw uniformly among the non-evaluated
-    valid configurations with splitmix64: r = next() mod (#non-evaluated),
-    and the r-th non-evaluated configuration in valid-list order is taken.
+  * Initial sampling handled by the session (n_init > 0) lasts until n_init
+    valid (finite) observations exist (Sec. III-E: invalid initial samples
+    are replaced until all are valid).  With init "lhs" / "maximin" the
+    session first hands out the design of oracle.sampling.initial_design
+    (skipping configurations already evaluated); otherwise, and after the
+    design, suggests draw uniformly among the non-evaluated valid
+    configurations with splitmix64: r = next() mod (#non-evaluated), and the
+    r-th non-evaluated configuration in valid-list order is taken.
 """
 from __future__ import annotations
 
@@ -27,6 +31,7 @@ import numpy as np
 
 from .bo_oracle import (AF_NAMES, acquisition, candidate_coords, contextual_variance_lambda,
                         gp_fit, gp_posterior, masked_topk, valid_list)
+from .sampling import initial_design
 from .selection import make_selector
 
 __all__ = ["OracleSession", "SplitMix64", "SuggestInfo"]
@@ -55,9 +60,10 @@ class SuggestInfo(dict):
 class OracleSession:
     def __init__(self, grids, invalid_mask=None, nu=1.5, lengthscale=1.5, jitter=1e-10,
                  af="ei", explore="cv", lambda_const=0.01, skip_threshold=5, rif=0.1,
-                 discount=None, normalize_y=True, n_init=0, seed=0):
+                 discount=None, normalize_y=True, n_init=0, seed=0, init="maximin", init_designs=100):
         self.grids = [np.asarray(g, dtype=np.float64) for g in grids]
         sizes = [len(g) for g in self.grids]
+        self.invalid_mask = invalid_mask
         self.flat, self.codes = valid_list(sizes, invalid_mask)
         self.coords = candidate_coords(self.grids, self.codes)
         self.N = len(self.flat)
@@ -68,6 +74,8 @@ class OracleSession:
         self.normalize_y = normalize_y
         self.n_init = n_init
         self.rng = SplitMix64(seed)
+        self.init, self.init_designs, self.seed = init, init_designs, seed
+        self.init_queue = None
         self.selector = make_selector(af, skip_threshold, discount, rif)
         self.mu_s = None
         self.mean_var_s = None
@@ -95,6 +103,11 @@ class OracleSession:
                 val = float(np.median(fy)) if fy else None
             if val is not None:
                 self.selector.credit(afs, val)
+
+    def _design(self, count):
+        """The initial design, drawn from the session's splitmix64 stream."""
+        return initial_design(self.grids, self.invalid_mask, count, self.init, self.init_designs,
+                              draw=self.rng.next)
 
     def _random_pick(self):
         free = np.flatnonzero(~self.visited)
@@ -131,7 +144,15 @@ class OracleSession:
         free = int(np.count_nonzero(~self.visited))
         if free == 0:
             raise StopIteration("search space exhausted")
-        if len(self.obs_y) < self.n_init or not self.finite_y():
+        if len(self.finite_y()) < self.n_init or not self.finite_y():
+            if self.init != "random" and self.n_init > 0:
+                if self.init_queue is None:
+                    count = min(self.n_init, len(self.visited))
+                    self.init_queue = list(self._design(count))
+                while self.init_queue and self.visited[self.init_queue[0]]:
+                    self.init_queue.pop(0)
+                if self.init_queue:
+                    return SuggestInfo(idx=int(self.init_queue.pop(0)), af=None, predicted=False)
             return SuggestInfo(idx=self._random_pick(), af=None, predicted=False)
         while self.queue:
             idx, afs = self.queue.pop(0)

@@ -22,6 +22,7 @@ ERRORS = {1: "BO_ERR_ARG", 2: "BO_ERR_INDEX", 3: "BO_ERR_DUPLICATE", 4: "BO_ERR_
 AF = {"ei": 0, "poi": 1, "pi": 1, "lcb": 2, "multi": 3, "advanced_multi": 4}
 AF_NAMES = {0: "ei", 1: "poi", 2: "lcb", -1: None}
 PRECISION = {"fp64": 0, "fp16x3": 1, "bf16x3": 2, "tf32": 3}
+INIT = {"random": 0, "lhs": 1, "maximin": 2}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -40,7 +41,8 @@ class SpaceDesc(C.Structure):
                 ("af", C.c_int32), ("explore", C.c_int32), ("lambda_const", C.c_double),
                 ("skip_threshold", C.c_int32), ("rif", C.c_double), ("discount", C.c_double),
                 ("y_norm", C.c_int32), ("precision", C.c_int32), ("n_max", C.c_int32),
-                ("n_init", C.c_int32), ("seed", C.c_uint64), ("alloc", ALLOC_FN),
+                ("n_init", C.c_int32), ("seed", C.c_uint64), ("init_mode", C.c_int32),
+                ("init_designs", C.c_int32), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p)]
 
 
@@ -95,6 +97,7 @@ class ServerStats(C.Structure):
 # every symbol include/bo_suggest.h declares, with (restype, argtypes)
 SIGNATURES = {
     "bo_space_desc_init": (None, [C.POINTER(SpaceDesc)]),
+    "bo_initial_design": (C.c_int, [C.POINTER(SpaceDesc), C.c_int32, C.c_void_p]),
     "bo_space_create": (C.c_int, [C.POINTER(SpaceDesc), C.POINTER(C.c_void_p)]),
     "bo_space_destroy": (C.c_int, [C.c_void_p]),
     "bo_valid_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
@@ -176,7 +179,8 @@ def _as_ptr(a, ctype):
 
 def make_desc(grids, invalid_mask=None, *, nu=1.5, lengthscale=1.5, jitter=1e-10, af="ei",
               explore="cv", lambda_const=0.01, skip_threshold=5, rif=0.1, discount=None,
-              normalize_y=True, precision="fp64", n_max=512, n_init=0, seed=0):
+              normalize_y=True, precision="fp64", n_max=512, n_init=0, seed=0, init="maximin",
+              init_designs=100):
     """A bo_space_desc for these arguments, and the arrays it points into."""
     grids = [np.ascontiguousarray(g, dtype=np.float64) for g in grids]
     d = len(grids)
@@ -203,7 +207,19 @@ def make_desc(grids, invalid_mask=None, *, nu=1.5, lengthscale=1.5, jitter=1e-10
     desc.n_max = n_max
     desc.n_init = n_init
     desc.seed = seed
+    desc.init_mode = INIT[init]
+    desc.init_designs = init_designs
     return desc, (grids, sizes, vals, mask)
+
+
+def initial_design(grids, invalid_mask=None, count=20, *, init="maximin", init_designs=100, seed=0):
+    """The initial sample (valid-list indices) a space with these arguments
+    draws; host computation, no device needed."""
+    desc, keep = make_desc(grids, invalid_mask, init=init, init_designs=init_designs, seed=seed)
+    out = np.zeros(count, dtype=np.int64)
+    _check(lib().bo_initial_design(C.byref(desc), count, out.ctypes.data))
+    del keep
+    return out
 
 
 class Space:

@@ -28,7 +28,7 @@ def nvcc() -> str:
 
 
 def _flags():
-    return ["-O3", "-std=c++17", ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O3",
+    return ["-O3", "-std=c++17", ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O3,-ffp-contract=off",
             f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}", "-DNDEBUG"]
 
 

@@ -257,7 +257,39 @@ int suggest_begin(bo_space* s, int64_t* idx_out, bo_suggest_info* info, bool* ne
   bo_suggest_info inf{};
   inf.af = -1;
   if (s->n_visited >= s->N) return fail(BO_ERR_EXHAUSTED, "every valid configuration was evaluated");
-  if ((int64_t)s->obs_y.size() < s->desc.n_init || s->n_fit == 0) {
+  if (s->n_fit < s->desc.n_init || s->n_fit == 0) {
+    // initial sample (Sec. III-E): the Latin hypercube design first, then
+    // random unobserved configurations until n_init valid observations exist
+    if (s->desc.init_mode != BO_INIT_RANDOM && s->desc.n_init > 0 && !s->init_built) {
+      s->init_built = true;
+      const int count = (int)std::min<int64_t>(s->desc.n_init, s->N);
+      std::vector<int64_t> design(count);
+      auto valid_of = [s](int64_t flat) -> int64_t {   // binary search: the valid list is in flat order
+        int64_t lo = 0, hi = s->N;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) / 2;
+          int64_t f = 0;
+          for (int p = 0; p < s->d; ++p) f = f * s->sizes[p] + s->codes[(size_t)p * s->N + mid];
+          if (f < flat) lo = mid + 1; else hi = mid;
+        }
+        if (lo == s->N) return -1;
+        int64_t f = 0;
+        for (int p = 0; p < s->d; ++p) f = f * s->sizes[p] + s->codes[(size_t)p * s->N + lo];
+        return f == flat ? lo : -1;
+      };
+      const int rc = initial_design(s->values, s->N, valid_of, count, s->desc.init_mode, s->desc.init_designs,
+                                    s->rng, design.data());
+      if (rc != BO_OK) return rc;
+      s->init_queue.assign(design.begin(), design.end());
+    }
+    while (!s->init_queue.empty() && s->visited[s->init_queue.front()]) s->init_queue.pop_front();
+    if (!s->init_queue.empty()) {
+      inf.idx = s->init_queue.front();
+      s->init_queue.pop_front();
+      *idx_out = inf.idx;
+      if (info) *info = inf;
+      return BO_OK;
+    }
     const int64_t free_count = s->N - s->n_visited;
     int64_t r = (int64_t)(splitmix64_next(s->rng) % (uint64_t)free_count);
     int64_t idx = -1;
@@ -339,6 +371,8 @@ void bo_space_desc_init(bo_space_desc* d) {
   d->y_norm = BO_YNORM_STANDARDIZE;
   d->precision = BO_PREC_FP64;
   d->n_max = BO_MAX_OBS;
+  d->init_mode = BO_INIT_MAXIMIN;
+  d->init_designs = 100;
 }
 
 const char* bo_last_error(void) { return g_err.c_str(); }
@@ -356,7 +390,8 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   if (D.explore != BO_EXPLORE_CV && D.explore != BO_EXPLORE_CONST) return fail(BO_ERR_ARG, "bad explore");
   if (D.precision < BO_PREC_FP64 || D.precision > BO_PREC_TF32) return fail(BO_ERR_ARG, "bad precision");
   if (D.n_max < 1 || D.n_max > BO_MAX_OBS) return fail(BO_ERR_ARG, "n_max not in [1, %d]", BO_MAX_OBS);
-  if (D.skip_threshold < 0 || D.n_init < 0) return fail(BO_ERR_ARG, "negative count");
+  if (D.skip_threshold < 0 || D.n_init < 0 || D.init_designs < 0) return fail(BO_ERR_ARG, "negative count");
+  if (D.init_mode < BO_INIT_RANDOM || D.init_mode > BO_INIT_MAXIMIN) return fail(BO_ERR_ARG, "bad init_mode");
   int64_t total = 1;
   for (int p = 0; p < D.d; ++p) {
     if (D.n_values[p] < 1 || D.n_values[p] > BO_MAX_VALUES || !D.values[p])

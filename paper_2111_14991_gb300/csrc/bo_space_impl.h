@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <deque>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -164,6 +165,8 @@ struct bo_space {
   bool cv_set = false;
   double mu_s = 0;
   uint64_t rng = 0;
+  std::deque<int64_t> init_queue;    // initial design not yet suggested (LHS / maximin)
+  bool init_built = false;
   bo::host::Selector sel;
   std::deque<bo::host::Pick> queue;
   std::map<int64_t, std::vector<int>> outstanding;
@@ -186,6 +189,14 @@ int cuda_fail(cudaError_t e, const char* what);
     cudaError_t e_ = (call);                            \
     if (e_ != cudaSuccess) return bo::host::cuda_fail(e_, #call); \
   } while (0)
+
+uint64_t splitmix64_next(uint64_t& state);
+// The initial sample of bo_initial_design: `count` distinct valid-list indices
+// into out, drawn from rng (advanced); valid_of maps a flat (row-major)
+// configuration index to its valid-list index, or -1 when restricted.
+int initial_design(const std::vector<std::vector<double>>& values, int64_t n_valid,
+                   const std::function<int64_t(int64_t)>& valid_of, int count, int mode, int designs,
+                   uint64_t& rng, int64_t* out);
 
 int dalloc(bo_space* s, size_t bytes, void** out);
 // Device bytes bo_space_create allocates for these sizes, and those a space holds.

@@ -152,11 +152,12 @@ def test_runtime_invalid_not_fitted():
     g.close()
 
 
-def test_init_phase_matches_splitmix64():
+@pytest.mark.parametrize("init", ["random", "lhs", "maximin"])
+def test_init_phase_matches_oracle(init):
     sp = W.config1_space()
     land = W.Landscape(sp, 7)
-    g = make(sp, n_init=12, seed=99)
-    o = O.OracleSession(sp.grids, sp.invalid, n_init=12, seed=99)
+    g = make(sp, n_init=12, seed=99, init=init, init_designs=40)
+    o = O.OracleSession(sp.grids, sp.invalid, n_init=12, seed=99, init=init, init_designs=40)
     for _ in range(15):
         gs, os_ = g.suggest(), o.suggest()
         assert gs["idx"] == os_["idx"]
@@ -164,6 +165,29 @@ def test_init_phase_matches_splitmix64():
         v = land(gs["idx"])
         g.observe(gs["idx"], v)
         o.observe(os_["idx"], v)
+    g.close()
+
+
+def test_init_phase_replaces_runtime_invalid_samples():
+    # Sec. III-E: initial samples that fail are replaced until n_init are valid
+    sp = W.paper_shaped_space("expdist")                 # about half the configurations fail at run time
+    land = W.Landscape(sp, 8)
+    g = make(sp, n_init=20, seed=5)
+    o = O.OracleSession(sp.grids, sp.invalid, n_init=20, seed=5)
+    n_finite = 0
+    for t in range(60):
+        gs, os_ = g.suggest(), o.suggest()
+        assert gs["idx"] == os_["idx"], t
+        assert gs["predicted"] == os_["predicted"]
+        if gs["predicted"]:
+            assert n_finite >= 20
+            break
+        v = land(gs["idx"])
+        n_finite += math.isfinite(v)
+        g.observe(gs["idx"], v)
+        o.observe(os_["idx"], v)
+    else:
+        raise AssertionError("initial phase did not end")
     g.close()
 
 

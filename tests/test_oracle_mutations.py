@@ -95,3 +95,45 @@ def test_dos_without_discount(monkeypatch):
             self.dos[a] = self.dos[a] + value
     monkeypatch.setattr(osel.MultiSelector, "credit", bad)
     _fails(T_sel.test_dos_definition)
+
+
+# ---- initial sample (Sec. III-E) ---------------------------------------------
+import oracle.sampling as osamp  # noqa: E402
+import test_oracle_sampling as T_samp  # noqa: E402
+
+
+def test_maximin_keeping_the_worst_design(monkeypatch):
+    orig = osamp.min_pair_sq_distance
+    monkeypatch.setattr(osamp, "min_pair_sq_distance", lambda pts: -orig(pts))
+    _fails(T_samp.test_maximin_improves_with_more_designs)
+
+
+def test_strata_ignored_plain_random_values(monkeypatch):
+    def bad(sizes, n, draw):
+        out = np.zeros((n, len(sizes)), dtype=np.int64)
+        for p in range(len(sizes)):
+            for i in range(n):
+                out[i, p] = draw() % sizes[p]
+        return out
+    monkeypatch.setattr(osamp, "latin_hypercube", bad)
+    monkeypatch.setattr(T_samp, "latin_hypercube", bad)
+    _fails(T_samp.test_latin_property_one_value_per_stratum, 0)
+
+
+def test_stratum_mapping_off_by_one(monkeypatch):
+    orig = osamp.latin_hypercube
+
+    def bad(sizes, n, draw):
+        v = orig(sizes, n, draw)
+        return np.minimum(v + 1, np.array(sizes) - 1)
+    monkeypatch.setattr(T_samp, "latin_hypercube", bad)
+    _fails(T_samp.test_each_stratum_holds_one_sample, 1)
+
+
+def test_restricted_samples_not_replaced(monkeypatch):
+    orig = osamp.initial_design
+
+    def bad(grids, mask, count, mode="maximin", designs=100, seed=0, draw=None):
+        return orig(grids, None, count, mode, designs, seed, draw)    # mask ignored
+    monkeypatch.setattr(T_samp, "initial_design", bad)
+    _fails(T_samp.test_restricted_samples_are_replaced_and_valid_ones_kept, "lhs")

@@ -89,3 +89,4 @@ def test_bo_beats_random_search(af):
         rand = [np.min(land.clean(rng.choice(sp.n_valid, 60, replace=False))) for _ in range(20)]
         wins += best_bo <= np.median(rand)
     assert wins == 3
+
