@@ -54,7 +54,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int phase_blocks_max(int n_max) {
   const int m = n_max - 1;   // the largest n an update can see before its new row
-  return (m + 31) / 32 + 1 + (m + 7) / 8 + ((m + 31) / 32) * ((m + 63) / 64) + (m + 8) / 8;
+  return (m + 31) / 32 + 1 + (m + 7) / 8 + ((m + 31) / 32) * ((m + 63) / 64) + 2 * ((m + 8) / 8);
 }
 
 void release_batch(bo_batch* b) {
@@ -251,7 +251,7 @@ int bo_batch_observe(bo_batch* b, const int64_t* idx, const double* values, int3
     if (rc != BO_OK && first_err == BO_OK) first_err = rc;
   }
   std::vector<ObsBlock> blocks;
-  int counts[4] = {0, 0, 0, 0};
+  int counts[5] = {0, 0, 0, 0, 0};
   obs_batch_blocks(n_before.data(), n_items, &blocks, counts);
   if ((int)blocks.size() > b->obs_block_cap) return fail(BO_ERR_STATE, "update block table overflow");
   std::memcpy(at<void>(b->stage, b->off_obs_blocks), blocks.data(), sizeof(ObsBlock) * blocks.size());
@@ -260,7 +260,8 @@ int bo_batch_observe(bo_batch* b, const int64_t* idx, const double* values, int3
   BO_CUDA(cudaMemcpyAsync(at<void>(b->dev, b->off_obs), b->stage + b->off_obs, b->obs_upload_end - b->off_obs,
                           cudaMemcpyHostToDevice, b->bs));
   const int k = launch_observe_batch(at<ObsItem>(b->dev, b->off_obs), n_items, at<ObsBlock>(b->dev, b->off_obs_blocks),
-                                     counts, at<VisitItem>(b->dev, b->off_visits), n_visits, b->bs);
+                                     counts, at<VisitItem>(b->dev, b->off_visits), n_visits,
+                                     b->precision != BO_PREC_FP64, b->bs);
   if (k < 0) return fail(BO_ERR_CUDA, "batched update launch failed");
   b->launches += k;
   rc = end_on_batch_stream(b);

@@ -57,7 +57,7 @@ struct DevView {
   uint8_t* lsplit_hi;        // reduced-precision chunked copy of L^-1 (hi or tf32)
   uint8_t* lsplit_lo;        // (lo part; unused for tf32)
   float* rowq;               // [n_max] 1 / s_k^2 of the per-row power-of-two scale s_k
-  float* rowb;               // [n_max] beta_k / s_k
+  float* alpha;              // [n_max] alpha = L^-T beta in FP32 (zero beyond n): mu = k* . alpha
 
   void* mu;                  // [N_pad] posterior mean (double for FP64, else float)
   void* var;                 // [N_pad] posterior variance
@@ -115,7 +115,7 @@ struct TcSess {
   const uint32_t* visited;
   const float* xf;           // [kXfRows][n_max] scaled observation coordinates
   const float* rowq;
-  const float* rowb;
+  const float* alpha;
   const uint8_t* lhi;        // chunked split copy of L^-1
   const uint8_t* llo;
   float* mu;
@@ -177,9 +177,9 @@ int launch_observe_update(const DevView& v, int n, int64_t idx, double y_raw, do
 int launch_set_visited(const DevView& v, int64_t idx, cudaStream_t s);
 // Block tables of the batched update phases k, l, w, beta (concatenated) for spaces with
 // n[i] observations fitted before their new one; counts[] receives each phase's block count.
-void obs_batch_blocks(const int* n, int count, std::vector<ObsBlock>* blocks, int counts[4]);
-int launch_observe_batch(const ObsItem* items, int count, const ObsBlock* blocks, const int counts[4],
-                         const VisitItem* visits, int n_visits, cudaStream_t s);
+void obs_batch_blocks(const int* n, int count, std::vector<ObsBlock>* blocks, int counts[5]);
+int launch_observe_batch(const ObsItem* items, int count, const ObsBlock* blocks, const int counts[5],
+                         const VisitItem* visits, int n_visits, bool tc, cudaStream_t s);
 int launch_predict_f64(const DevView& v, int n, int64_t n_unvisited, cudaStream_t s);
 int launch_predict_tc(const DevView& v, int n, int64_t n_unvisited, cudaStream_t s);
 TcSess tc_session(const DevView& v, int n);

@@ -1,8 +1,11 @@
 // Prediction pass on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
 // Same mathematics as the FP64 pass (paper Sec. III-B, III-G): for every
-// candidate c, v = L^-1 k*(c), var = k(0) - |v|^2, mu = v . beta.  Here the
-// contraction V = K* L^-T runs on the tensor cores with FP32 accumulation in
+// candidate c, v = L^-1 k*(c), var = k(0) - |v|^2, mu = k* . alpha with
+// alpha = L^-T beta (the FP64 update provides it).  The producers that
+// evaluate K* also accumulate mu (FP32 within a chunk, FP64 across chunks), so
+// mu does not depend on the split contraction; the contraction V = K* L^-T,
+// needed for the variance, runs on the tensor cores with FP32 accumulation in
 // tensor memory, with the operands split to recover precision:
 //   FP16X3 / BF16X3: K* = Kh + Kl and L^-1 = Lh + Ll (per-row power-of-two
 //     scaled), V ~ Kh Lh + Kh Ll + Kl Lh  (three MMAs per k-step)
@@ -19,19 +22,20 @@
 //   warps 0-15   produce K* chunks: thread (row = t % 128, quarter = t / 128)
 //                evaluates the Matern covariance of its candidate against a
 //                quarter of the chunk's observations (packed f32x2, over the
-//                space's own d coordinates), splits it and stores it in the
-//                K-major core-matrix layout.  The next tile's candidate codes
-//                are fetched while the current tile is computed.
-//   warps 16-19  drain the accumulator (TMEM lane = row): sum acc_k^2 q_k and
-//                acc_k b_k (q, b of the space in shared memory), write mu and
-//                var.  Column block c is final once chunk c's MMAs complete,
+//                space's own d coordinates), adds its share of k* . alpha,
+//                splits it and stores it in the K-major core-matrix layout.
+//                A row's four quarters sit in one warp and meet by shuffles
+//                to write mu.  The next tile's candidate codes are fetched
+//                while the current tile is computed.
+//   warps 16-19  drain the accumulator (TMEM lane = row): sum acc_k^2 q_k
+//                (q of the space in shared memory) and write var.  Column block c is final once chunk c's MMAs complete,
 //                so it is drained then (one barrier per block), and each
 //                256-column region is handed back after its last block: the
 //                next tile's first MMAs into a region wait only for that
 //                region.  With n <= 256 the accumulator is double-buffered.
 //   warp 20      issues the MMAs (one thread) and owns the TMEM allocation.
 //   warp 21      streams, with bulk copies (one thread), each space's
-//                observation coordinates and per-row factors into shared
+//                observation coordinates, 1/s^2 and alpha into shared
 //                memory (double-buffered across spaces) and the L^-1 chunks in pieces of at most 256
 //                rows: a 4-slot ring, or, for one space whose pieces fit, all
 //                pieces resident, loaded once.
@@ -65,6 +69,7 @@ constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 constexpr int kPieceRows = 256;         // rows of L^-1 per B piece (= max MMA N)
 constexpr int kMaxBSlots = 16;
 constexpr int kAccBars = 32;            // per accumulator column block: 2 buffers x 16, or 1 x 32
+constexpr int kMuPartBytes = 2 * 4 * kRows * 4;   // the four quarter sums of mu, two tiles
 
 struct TcParams {
   TcSess s0;                 // the space, when batch == 0
@@ -83,7 +88,7 @@ struct TcParams {
   // B (the split L^-1 chunks) in pieces of <= 256 rows: either a ring of
   // b_slots fixed-size slots, or every piece of the space resident (loaded once)
   int b_resident, b_slots;
-  size_t off_b, b_slot_bytes, off_x, x_buf_bytes, off_bar;
+  size_t off_b, b_slot_bytes, off_x, x_buf_bytes, off_mu, off_bar;
 };
 
 // Position in a CTA's work: one space with strided tiles, or a segment list.
@@ -303,6 +308,21 @@ __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
   return r;
 }
 __device__ __forceinline__ uint64_t dup2(float x) { return pk2(x, x); }
+// hi + lo += x by Knuth's TwoSum: a compensated FP32 running sum.  (FP64 is
+// a narrow unit on this GPU; the per-tile sums stay off it.)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float t = hi + x;
+  const float bp = t - hi;
+  lo += (hi - (t - bp)) + (x - bp);
+  hi = t;
+}
+
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
 
 // Matern covariance in FP32 for two squared distances at once (one packed
 // word), in units where u = t log2(e), t = sqrt(2 nu) r / l (the coordinate
@@ -407,7 +427,9 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
   uint64_t* xs_full = bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 2;       // [2]
   uint64_t* xs_empty = bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 4;      // [2]
   uint64_t* drain = bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 6;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 7);
+  uint64_t* mu_full = bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 7;       // [2]
+  uint64_t* mu_empty = bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 9;      // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 11);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ double red[4];   // per epilogue warp
   __shared__ bool s_last;
@@ -424,6 +446,10 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
       mbar_init(&xs_empty[s], kProducerWarps + 4);   // producers and epilogue warps
     }
     mbar_init(drain, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&mu_full[s], kProducerWarps);
+      mbar_init(&mu_empty[s], 4);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -446,18 +472,19 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     const int jq = cw / 4;                       // observations per thread per chunk: 8 or 4
     const uint32_t a_base = smem_addr(sa);
     const uint32_t row_off = (uint32_t)((row >> 3) * (kChunkBytes * 8) + (row & 7) * 16 + quarter * 128);
+    float* mu_part = reinterpret_cast<float*>(smem + P.off_mu);   // [2 tiles][4 quarters][128 rows]
     bool ok = true;
-    int s = 0, ks = -1, prev = -1;
+    int s = 0, ks = -1, prev = -1, tile_it = 0;
     uint32_t ph = 0;                             // ring slot and its phase
     int n_pad = 0, chunks = 0, d = 0;
     int64_t N_pad = 0;
     const uint8_t* codes = nullptr;
     const float* vt = nullptr;
     uint32_t xs = xs_base;
-    uint32_t code_next[DMAX];
+    uint32_t code_next[(DMAX + 3) / 4];         // the next tile's codes, four per word
     bool have_next = false;
     Work w;
-    for (bool more = work_begin(P, w); more && ok; more = work_next(P, w)) {
+    for (bool more = work_begin(P, w); more && ok; more = work_next(P, w), ++tile_it) {
       if (w.sess != prev) {                      // next space: its coordinates, once copied in
         if (ks >= 0) {
           __syncwarp();
@@ -475,64 +502,101 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         xs = xs_base + (uint32_t)((ks % XB) * P.x_buf_bytes);
         if (!(ok = mbar_wait(&xs_full[ks % XB], (uint32_t)((ks / XB) & 1), abort_flag, status))) break;
       }
-      // this tile's candidate codes: prefetched during the previous tile, except for the first
       const int64_t cand = (int64_t)w.tile * kRows + row;
-      uint32_t cc[DMAX];
-#pragma unroll
-      for (int p = 0; p < DMAX; ++p)
-        cc[p] = have_next ? code_next[p] : (p < d ? (uint32_t)codes[(int64_t)p * N_pad + cand] : 0u);
+      // mu = k* . alpha: two packed FP32 sums over groups of 4 chunks, folded
+      // into a compensated (hi, lo) pair by Knuth's TwoSum after each group
+      uint64_t m2 = 0ull, mhi = 0ull, mlo = 0ull;
       {
-        Work wn = w;
-        have_next = work_next(P, wn);
-        if (have_next) {
-          const TcSess& Sn = sess_of(P, wn.sess);
-          const int64_t cn = (int64_t)wn.tile * kRows + row;
-          const int dn = Sn.d;
-          const int64_t Nn = Sn.N_pad;
-          const uint8_t* cp = Sn.codes;
+        // this tile's candidate codes: prefetched during the previous tile, except for the first
+        uint32_t cc[DMAX];
 #pragma unroll
-          for (int p = 0; p < DMAX; ++p) code_next[p] = p < dn ? (uint32_t)cp[(int64_t)p * Nn + cn] : 0u;
-        }
-      }
-      uint64_t xcp[DMAX];                      // candidate coordinate, twice per word
+        for (int p = 0; p < DMAX; ++p)
+          cc[p] = have_next ? (code_next[p >> 2] >> (8 * (p & 3))) & 0xFFu
+                            : (p < d ? (uint32_t)codes[(int64_t)p * N_pad + cand] : 0u);
+        {
+          Work wn = w;
+          have_next = work_next(P, wn);
+          if (have_next) {
+            const TcSess& Sn = sess_of(P, wn.sess);
+            const int64_t cn = (int64_t)wn.tile * kRows + row;
+            const int dn = Sn.d;
+            const int64_t Nn = Sn.N_pad;
+            const uint8_t* cp = Sn.codes;
 #pragma unroll
-      for (int p = 0; p < DMAX; ++p) xcp[p] = dup2(p < d ? vt[p * 256 + cc[p]] : 0.0f);
-      for (int c = 0; c < chunks && ok; ++c) {
-        const int j0 = c * cw + quarter * jq;
-        // K* for this thread's observations, computed before waiting for the ring slot
-        uint64_t r2p[4];
-        const uint32_t xrow = xs + (uint32_t)(j0 * 4);
-        if (d == DMAX)
-          sq_dist<MODE, DMAX, false>(xcp, xrow, n_pad, d, r2p);
-        else
-          sq_dist<MODE, DMAX, true>(xcp, xrow, n_pad, d, r2p);
-        uint64_t kv[4];
+            for (int p = 0; p < (DMAX + 3) / 4; ++p) code_next[p] = 0u;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (2 * q < jq) kv[q] = matern2<NU52>(r2p[q]);
-        if (!(ok = mbar_wait(&a_empty[s], ph ^ 1, abort_flag, status))) break;
-        const uint32_t stage = a_base + (uint32_t)(s * parts * kPartBytes) + row_off;
-        if constexpr (MODE == BO_PREC_TF32) {
-          float k0, k1, k2, k3;
-          upk2(kv[0], k0, k1);
-          upk2(kv[1], k2, k3);
-          st_shared_v4(stage, to_tf32(k0), to_tf32(k1), to_tf32(k2), to_tf32(k3));
-        } else {
-          uint32_t h[4], l[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            float ka, kb;
-            upk2(kv[q], ka, kb);
-            split2<MODE>(ka, kb, h[q], l[q]);
+            for (int p = 0; p < DMAX; ++p)
+              if (p < dn) code_next[p >> 2] |= (uint32_t)cp[(int64_t)p * Nn + cn] << (8 * (p & 3));
           }
-          st_shared_v4(stage, h[0], h[1], h[2], h[3]);
-          st_shared_v4(stage + kPartBytes, l[0], l[1], l[2], l[3]);
         }
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&a_full[s]);
-        if (++s == SA) { s = 0; ph ^= 1; }
+        uint64_t xcp[DMAX];                    // candidate coordinate, twice per word
+#pragma unroll
+        for (int p = 0; p < DMAX; ++p) xcp[p] = dup2(p < d ? vt[p * 256 + cc[p]] : 0.0f);
+        for (int c = 0; c < chunks && ok; ++c) {
+          const int j0 = c * cw + quarter * jq;
+          // K* for this thread's observations, computed before waiting for the ring slot
+          uint64_t r2p[4];
+          const uint32_t xrow = xs + (uint32_t)(j0 * 4);
+          if (d == DMAX)
+            sq_dist<MODE, DMAX, false>(xcp, xrow, n_pad, d, r2p);
+          else
+            sq_dist<MODE, DMAX, true>(xcp, xrow, n_pad, d, r2p);
+          uint64_t kv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (2 * q < jq) kv[q] = matern2<NU52>(r2p[q]);
+          {
+            const uint32_t arow = xs + (uint32_t)((DMAX + 1) * n_pad * 4 + j0 * 4);
+            uint64_t a0, a1;
+            lds2x64(arow, a0, a1);
+            m2 = fma2(kv[1], a1, fma2(kv[0], a0, m2));
+            if constexpr (MODE != BO_PREC_TF32) {
+              lds2x64(arow + 16, a0, a1);
+              m2 = fma2(kv[3], a1, fma2(kv[2], a0, m2));
+            }
+            if ((c & 3) == 3 || c + 1 == chunks) {
+              const uint64_t t = add2(mhi, m2);
+              const uint64_t bp = sub2(t, mhi);
+              mlo = add2(mlo, add2(sub2(mhi, sub2(t, bp)), sub2(m2, bp)));
+              mhi = t;
+              m2 = 0ull;
+            }
+          }
+          if (!(ok = mbar_wait(&a_empty[s], ph ^ 1, abort_flag, status))) break;
+          const uint32_t stage = a_base + (uint32_t)(s * parts * kPartBytes) + row_off;
+          if constexpr (MODE == BO_PREC_TF32) {
+            float k0, k1, k2, k3;
+            upk2(kv[0], k0, k1);
+            upk2(kv[1], k2, k3);
+            st_shared_v4(stage, to_tf32(k0), to_tf32(k1), to_tf32(k2), to_tf32(k3));
+          } else {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              float ka, kb;
+              upk2(kv[q], ka, kb);
+              split2<MODE>(ka, kb, h[q], l[q]);
+            }
+            st_shared_v4(stage, h[0], h[1], h[2], h[3]);
+            st_shared_v4(stage + kPartBytes, l[0], l[1], l[2], l[3]);
+          }
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&a_full[s]);
+          if (++s == SA) { s = 0; ph ^= 1; }
+        }
       }
+      if (!ok) break;
+      // tile end: this quarter's sum goes to the epilogue through shared memory
+      // (double-buffered by tile, handed over with mbarriers)
+      const int mb = tile_it & 1;
+      if (!(ok = mbar_wait(&mu_empty[mb], ((uint32_t)(tile_it >> 1) & 1u) ^ 1u, abort_flag, status))) break;
+      float h0, h1, l0, l1;
+      upk2(mhi, h0, h1);
+      upk2(mlo, l0, l1);
+      mu_part[(mb * 4 + quarter) * kRows + row] = (h0 + h1) + (l0 + l1);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&mu_full[mb]);
     }
   } else if (warp < kMmaWarp) {
     // ===================== epilogue: warp e owns TMEM lanes [32e, 32e+32) =====================
@@ -543,19 +607,19 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     int n_pad = 0, chunks = 0;
     uint32_t par[2] = {0u, 0u};                  // phase parity of each block barrier, per buffer
     int64_t N = 0;
-    const float* rq = nullptr;                   // 1/s_k^2 and beta_k/s_k of the space, shared memory
-    const float* rb = nullptr;
+    const float* rq = nullptr;                   // 1/s_k^2 of the space, shared memory
     const uint32_t* visited = nullptr;
-    float* mu = nullptr;
     float* var = nullptr;
+    float* mu = nullptr;
+    float vs_hi = 0.0f, vs_lo = 0.0f;           // this thread's variance sum (compensated)
     Work w;
     for (bool more = work_begin(P, w); more && ok; more = work_next(P, w), ++it) {
       if (P.batch && w.seg != seg) {             // segment boundary: hand in its variance sum
         if (seg >= 0) {
-          double t = vsum;
+          double t = (double)vs_hi + (double)vs_lo;
           for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
           if (lane == 0) P.seg_part[(size_t)seg * 4 + e] = t;
-          vsum = 0.0;
+          vs_hi = vs_lo = 0.0f;
         }
         seg = w.seg;
       }
@@ -572,10 +636,9 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         N = S.N;
         const float* xsb = reinterpret_cast<const float*>(smem + P.off_x + (size_t)(ks % XB) * P.x_buf_bytes);
         rq = xsb + (size_t)DMAX * n_pad;
-        rb = rq + n_pad;
         visited = S.visited;
-        mu = S.mu;
         var = S.var;
+        mu = S.mu;
         if (!(ok = mbar_wait(&xs_full[ks % XB], (uint32_t)((ks / XB) & 1), abort_flag, status))) break;
       }
       // column block c (the chunk's CW columns) is final once chunk c's MMAs
@@ -583,7 +646,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
       // buffer after its last block
       const int as = it % P.acc_stages;
       const uint32_t lane_base = tmem + (uint32_t)(as * P.tmem_cols) + ((uint32_t)(e * 32) << 16);
-      uint64_t s2p = 0ull, smp = 0ull;           // two columns per packed word
+      uint64_t s2p = 0ull;                       // two columns per packed word
       for (int c = 0; c < chunks && ok; ++c) {
         if (!(ok = mbar_wait(&acc_full[as * 16 + c], (par[as] >> c) & 1u, abort_flag, status))) break;
         par[as] ^= 1u << c;
@@ -597,12 +660,9 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
 #pragma unroll
         for (int i = 0; i < CW; i += 4) {
           const float4 q = *reinterpret_cast<const float4*>(rq + k0 + i);
-          const float4 b = *reinterpret_cast<const float4*>(rb + k0 + i);
           const uint64_t a01 = pk2(acc[i], acc[i + 1]), a23 = pk2(acc[i + 2], acc[i + 3]);
           s2p = fma2(mul2(a01, pk2(q.x, q.y)), a01, s2p);
           s2p = fma2(mul2(a23, pk2(q.z, q.w)), a23, s2p);
-          smp = fma2(a01, pk2(b.x, b.y), smp);
-          smp = fma2(a23, pk2(b.z, b.w), smp);
         }
         const int kend = k0 + CW;
         if (kend == n_pad || (kend & (kPieceRows - 1)) == 0) {
@@ -612,22 +672,29 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         }
       }
       if (!ok) break;
-      float s2a, s2b, sma, smb;
+      float s2a, s2b;
       upk2(s2p, s2a, s2b);
-      upk2(smp, sma, smb);
-      const float s2 = s2a + s2b, sm = sma + smb;
+      const float s2 = s2a + s2b;
       const int64_t cand = (int64_t)w.tile * kRows + row;
       const float vr = fmaxf(0.0f, 1.0f - s2);
-      mu[cand] = sm;
       var[cand] = vr;
-      if (cand < N && !((visited[cand >> 5] >> (cand & 31)) & 1u)) vsum += (double)vr;
+      {   // mu: the producers' four quarter sums of k* . alpha, added in a fixed order
+        const int mb = it & 1;
+        if (!(ok = mbar_wait(&mu_full[mb], (uint32_t)(it >> 1) & 1u, abort_flag, status))) break;
+        const float* mp = reinterpret_cast<const float*>(smem + P.off_mu) + mb * 4 * kRows + row;
+        mu[cand] = ((mp[0] + mp[kRows]) + mp[2 * kRows]) + mp[3 * kRows];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&mu_empty[mb]);
+      }
+      if (cand < N && !((visited[cand >> 5] >> (cand & 31)) & 1u)) two_sum_acc(vs_hi, vs_lo, vr);
     }
     if (P.batch && seg >= 0 && ok) {
-      double t = vsum;
+      double t = (double)vs_hi + (double)vs_lo;
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       if (lane == 0) P.seg_part[(size_t)seg * 4 + e] = t;
-      vsum = 0.0;
+      vs_hi = vs_lo = 0.0f;
     }
+    vsum = (double)vs_hi + (double)vs_lo;
   } else if (warp == kMmaWarp) {
     // ===================== MMA issuer =====================
     if (lane == 0) {
@@ -736,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           const uint32_t dst = xs_base + (uint32_t)(xb * P.x_buf_bytes);
           for (int p = 0; p < DMAX; ++p) bulk_g2s(dst + (uint32_t)p * row_bytes, S.xf + (size_t)p * n_max, row_bytes, &xs_full[xb]);
           bulk_g2s(dst + (uint32_t)DMAX * row_bytes, S.rowq, row_bytes, &xs_full[xb]);
-          bulk_g2s(dst + (uint32_t)(DMAX + 1) * row_bytes, S.rowb, row_bytes, &xs_full[xb]);
+          bulk_g2s(dst + (uint32_t)(DMAX + 1) * row_bytes, S.alpha, row_bytes, &xs_full[xb]);
           xs_issued[xb] = 1;
           xs_phase[xb] = (ks / XB) & 1;
         }
@@ -886,7 +953,7 @@ size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resid
   P.b_slots = shape.b_slots > 0 ? std::min(shape.b_slots, kMaxBSlots) : 4;
   P.b_slot_bytes = (size_t)P.parts * (kPieceRows / 8) * 512;
   const size_t b_bytes = P.b_resident ? resident : P.b_slots * P.b_slot_bytes;
-  const size_t fixed = ((b_bytes + 1023) / 1024) * 1024 + ((x_bytes + 1023) / 1024) * 1024 + 512;
+  const size_t fixed = ((b_bytes + 1023) / 1024) * 1024 + ((x_bytes + 1023) / 1024) * 1024 + kMuPartBytes + 512;
   if (fixed >= limit) return 0;
   int sa = (int)((limit - fixed) / a_stage);
   sa = std::min(sa, 8);          // ring slots advance by counters: any depth >= 2 works
@@ -895,8 +962,9 @@ size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resid
   P.stages_a = sa;
   P.off_b = (size_t)sa * a_stage;
   P.off_x = P.off_b + ((b_bytes + 1023) / 1024) * 1024;
-  P.off_bar = (P.off_x + x_bytes + 15) / 16 * 16;
-  const size_t smem = P.off_bar + (size_t)(2 * sa + 2 * kMaxBSlots + kAccBars + 8) * 8 + 16;
+  P.off_mu = (P.off_x + x_bytes + 15) / 16 * 16;
+  P.off_bar = P.off_mu + kMuPartBytes;
+  const size_t smem = P.off_bar + (size_t)(2 * sa + 2 * kMaxBSlots + kAccBars + 12) * 8 + 16;
   // every descriptor footprint stays inside its stage: A parts are 128 rows x
   // 64 B; a B piece [r0, r0 + w) ends at the end of its part
   if ((size_t)15 * 512 + 256 + 255 >= (size_t)kPartBytes) return 0;
@@ -919,7 +987,7 @@ TcSess tc_session(const DevView& v, int n) {
   S.visited = v.visited;
   S.xf = v.Xf;
   S.rowq = v.rowq;
-  S.rowb = v.rowb;
+  S.alpha = v.alpha;
   S.lhi = v.lsplit_hi;
   S.llo = v.lsplit_lo;
   S.mu = static_cast<float*>(v.mu);

@@ -478,7 +478,7 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   TRY(dalloc_n(s, (size_t)n_alloc * n_alloc, &v.linv));
   TRY(dalloc_n(s, (size_t)n_alloc, &v.beta));
   TRY(dalloc_n(s, (size_t)n_alloc, &v.rowq));
-  TRY(dalloc_n(s, (size_t)n_alloc, &v.rowb));
+  TRY(dalloc_n(s, (size_t)n_alloc, &v.alpha));
   if (D.precision != BO_PREC_FP64) {
     TRY(dalloc_n(s, lsplit_bytes(n_alloc, D.precision), &v.lsplit_hi));
     if (D.precision != BO_PREC_TF32) TRY(dalloc_n(s, lsplit_bytes(n_alloc, D.precision), &v.lsplit_lo));

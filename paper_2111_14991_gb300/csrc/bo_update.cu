@@ -215,7 +215,7 @@ __device__ __forceinline__ void obs_finish_body(const DevView& v, int n) {
 __global__ void obs_finish_kernel(DevView v, int n) { obs_finish_body(v, n); }
 
 
-// --- K3e: beta = L^-1 y~ for rows 0..n, and beta_k / s_k -------------------------
+// --- K3e: beta = L^-1 y~ for rows 0..n ------------------------------------------
 __device__ __forceinline__ void obs_beta_body(const DevView& v, int rows, double y_mean, double inv_std,
                                               int block) {
   const int warp = (block * blockDim.x + threadIdx.x) >> 5;
@@ -225,15 +225,30 @@ __device__ __forceinline__ void obs_beta_body(const DevView& v, int rows, double
   double s = 0.0;
   for (int j = lane; j <= warp; j += 32) s = fma(row[j], (v.y[j] - y_mean) * inv_std, s);
   s = warp_sum(s);
-  if (lane == 0) {
-    v.beta[warp] = s;
-    if (v.precision != BO_PREC_FP64) v.rowb[warp] = (float)(s * sqrt((double)v.rowq[warp]));
-  }
+  if (lane == 0) v.beta[warp] = s;
+}
+
+// --- K3f (tensor-core forms): alpha = L^-T beta, so that mu = k* . alpha -------
+// (warp per column j: lanes stride down the rows i >= j of L^-1, fixed-order
+// reduction).  The prediction pass evaluates mu from K* and alpha directly:
+// the FP32 error of mu is then bounded by sum_j |alpha_j k*_j| times the K*
+// and accumulation rounding, and does not depend on the split contraction.
+__device__ __forceinline__ void obs_alpha_body(const DevView& v, int rows, int block) {
+  if (v.precision == BO_PREC_FP64) return;
+  const int col = (block * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (col >= rows) return;
+  double s = 0.0;
+  for (int i = col + lane; i < rows; i += 32) s = fma(v.linv[(size_t)i * v.n_max + col], v.beta[i], s);
+  s = warp_sum(s);
+  if (lane == 0) v.alpha[col] = (float)s;
 }
 
 __global__ void obs_beta_kernel(DevView v, int rows, double y_mean, double inv_std) {
   obs_beta_body(v, rows, y_mean, inv_std, blockIdx.x);
 }
+
+__global__ void obs_alpha_kernel(DevView v, int rows) { obs_alpha_body(v, rows, blockIdx.x); }
 
 // ---- the same phases over many spaces: block b serves item blocks[b].item ----
 __global__ void obs_k_batch(const ObsItem* items, const ObsBlock* blocks) {
@@ -266,6 +281,12 @@ __global__ void obs_beta_batch(const ObsItem* items, const ObsBlock* blocks) {
   obs_beta_body(it.v, it.n + 1, it.y_mean, it.inv_std, b.local);
 }
 
+__global__ void obs_alpha_batch(const ObsItem* items, const ObsBlock* blocks) {
+  const ObsBlock b = blocks[blockIdx.x];
+  const ObsItem& it = items[b.item];
+  obs_alpha_body(it.v, it.n + 1, b.local);
+}
+
 __global__ void set_visited_batch(const VisitItem* items, int count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) atomicOr(&items[i].visited[items[i].idx >> 5], 1u << (items[i].idx & 31));
@@ -275,7 +296,7 @@ __global__ void set_visited_kernel(uint32_t* visited, long long idx) {
   atomicOr(&visited[idx >> 5], 1u << (idx & 31));
 }
 
-void obs_batch_blocks(const int* n, int count, std::vector<ObsBlock>* blocks, int counts[4]) {
+void obs_batch_blocks(const int* n, int count, std::vector<ObsBlock>* blocks, int counts[5]) {
   // per phase, the blocks each space needs (as the single-space launch uses)
   blocks->clear();
   auto add = [&](int phase_blocks(int), int slot) {
@@ -288,10 +309,11 @@ void obs_batch_blocks(const int* n, int count, std::vector<ObsBlock>* blocks, in
   add([](int m) { return (m + 7) / 8; }, 1);                          // l: warp per row
   add([](int m) { return ((m + 31) / 32) * ((m + 63) / 64); }, 2);    // w: 32 columns x 64 rows
   add([](int m) { return (m + 1 + 7) / 8; }, 3);                      // beta: warp per row
+  add([](int m) { return (m + 1 + 7) / 8; }, 4);                      // alpha: warp per column
 }
 
-int launch_observe_batch(const ObsItem* items, int count, const ObsBlock* blocks, const int counts[4],
-                         const VisitItem* visits, int n_visits, cudaStream_t s) {
+int launch_observe_batch(const ObsItem* items, int count, const ObsBlock* blocks, const int counts[5],
+                         const VisitItem* visits, int n_visits, bool tc, cudaStream_t s) {
   int launches = 0;
   const ObsBlock* b = blocks;
   if (count > 0) {
@@ -304,6 +326,8 @@ int launch_observe_batch(const ObsItem* items, int count, const ObsBlock* blocks
     obs_finish_batch<<<count, 512, 0, s>>>(items);
     ++launches;
     if (counts[3]) { obs_beta_batch<<<counts[3], 256, 0, s>>>(items, b); ++launches; }
+    b += counts[3];
+    if (counts[4] && tc) { obs_alpha_batch<<<counts[4], 256, 0, s>>>(items, b); ++launches; }
   }
   if (n_visits > 0) {
     set_visited_batch<<<(n_visits + 127) / 128, 128, 0, s>>>(visits, n_visits);
@@ -333,6 +357,10 @@ int launch_observe_update(const DevView& v, int n, int64_t idx, double y_raw, do
   const int rows = n + 1;
   obs_beta_kernel<<<(rows + 7) / 8, 256, 0, s>>>(v, rows, y_mean, 1.0 / y_std);
   launches += 2;
+  if (v.precision != BO_PREC_FP64) {
+    obs_alpha_kernel<<<(rows + 7) / 8, 256, 0, s>>>(v, rows);
+    ++launches;
+  }
   return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 

@@ -1,14 +1,15 @@
 """Tensor-core (tcgen05) prediction vs the FP64 oracle, through the C ABI.
 
-FP16X3 meets the reduced-precision bar (1e-3 on the prior scale) on sigma at
-the full-size states (configs 2 and 3).  Its mean misses it by ~2x: the
-posterior mean amplifies the relative error of K* by sum_j |alpha_j k*_j|
-(~5e3 here), and K* is evaluated in FP32 (~3e-7 relative through exp and
-sqrt); the strict check is kept as an expected failure with that reason, and
-an envelope guards against regressions.  BF16X3 and TF32 are the other forms
-of the contraction: their error is a property of the format on
+The posterior mean is accumulated as k* . alpha next to the K* evaluation
+(FP32 within a chunk, compensated across chunks), so it does not depend on the
+split contraction: every reduced mode meets the 1e-3 bar on mu at the
+full-size states (configs 2 and 3).  The variance comes from the contraction:
+FP16X3 meets the bar on sigma there; BF16X3 and TF32 are the other forms of
+the contraction, whose sigma error is a property of the format on
 ill-conditioned K (measured per configuration and reported), so they are
-checked against an envelope only.
+checked against an envelope.  Config 1 (80 noisy observations, cond(K) ~
+1.4e7) amplifies FP32 rounding of K* by sum_j |alpha_j k*_j| ~ 1e5, beyond
+what any FP32 K* can meet: it is checked against an envelope too.
 """
 import numpy as np
 import pytest
@@ -19,8 +20,8 @@ from tolerances import REDUCED, assert_close, pick_ok, scaled_err
 
 pytestmark = pytest.mark.gpu
 
-# measured max scaled error x ~2.5: full-size states (configs 2, 3) and config 1 (cond(K) ~ 1.4e7)
-ENVELOPE = {"fp16x3": 5e-3, "bf16x3": 5e-2, "tf32": 2.0}
+# sigma, measured max scaled error x ~2.5 at the full-size states; config 1 (cond(K) ~ 1.4e7) for both
+ENVELOPE = {"fp16x3": 5e-3, "bf16x3": 5e-2, "tf32": 0.5}
 ENVELOPE_CFG1 = {"fp16x3": 2e-2, "bf16x3": 0.5, "tf32": 30.0}
 
 
@@ -105,21 +106,31 @@ def oracle_full(sp, idx, y, chunk=100_000):
     return fit, np.concatenate(mus), np.concatenate(vs)
 
 
+ORACLE_FULL = {}
+
+
 @pytest.mark.parametrize("cfg,n", [(2, 220), (3, 512)])
-def test_fp16x3_full_size(cfg, n):
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3", "tf32"])
+def test_full_size(cfg, n, precision):
     """Full-size state in the launch configuration the bench times: every
     candidate on the GPU; the oracle on every candidate too (chunked), for the
-    errors on a seeded 10k subsample and the EI argmax."""
+    errors on a seeded 10k subsample and the EI argmax.  mu meets the 1e-3 bar
+    in every mode, sigma in FP16X3."""
     sp = W.config2_space() if cfg == 2 else W.config3_space()
-    g, idx, y = state(sp, n, 0, "fp16x3", n_max=max(n, 32))
+    g, idx, y = state(sp, n, 0, precision, n_max=max(n, 32))
     mu, var = g.predict()
-    fit, rmu, rvar = oracle_full(sp, idx, y)
+    if cfg not in ORACLE_FULL:
+        ORACLE_FULL[cfg] = oracle_full(sp, idx, y)
+    fit, rmu, rvar = ORACLE_FULL[cfg]
     rng = np.random.default_rng(cfg)
     sub = rng.choice(sp.n_valid, 10_000, replace=False)
-    em = assert_close(mu[sub], rmu[sub], rel=ENVELOPE["fp16x3"], floor=1.0, what="mu")
-    es = assert_close(np.sqrt(var[sub]), np.sqrt(rvar[sub]), what="sigma", **REDUCED)
-    print(f"config {cfg} fp16x3: max scaled error mu {em:.2e} sigma {es:.2e}")
-    FULL[cfg] = (mu[sub], rmu[sub])
+    em = assert_close(mu[sub], rmu[sub], what="mu", **REDUCED)
+    if precision == "fp16x3":
+        es = assert_close(np.sqrt(var[sub]), np.sqrt(rvar[sub]), what="sigma", **REDUCED)
+    else:
+        es = assert_close(np.sqrt(var[sub]), np.sqrt(rvar[sub]), rel=ENVELOPE[precision], floor=1.0,
+                          what="sigma")
+    print(f"config {cfg} {precision}: max scaled error mu {em:.2e} sigma {es:.2e}")
     mask = np.ones(sp.n_valid, bool)
     mask[idx] = False
     ymin = (y.min() - y.mean()) / y.std()
@@ -128,21 +139,9 @@ def test_fp16x3_full_size(cfg, n):
     best = O.masked_argmax(scores, mask)
     gs = g.suggest()
     assert not np.isin(gs["idx"], idx)
-    assert pick_ok(scores, gs["idx"], best, rel=ENVELOPE["fp16x3"], floor=1.0)
+    tol = REDUCED if precision == "fp16x3" else dict(rel=ENVELOPE[precision], floor=1.0)
+    assert pick_ok(scores, gs["idx"], best, **tol)
     g.close()
-
-
-FULL = {}
-
-
-@pytest.mark.xfail(strict=False, reason="posterior mean amplifies the FP32 evaluation error of "
-                   "K* by sum_j |alpha_j k*_j| ~ 5e3: measured ~1.7e-3 against the 1e-3 bar")
-@pytest.mark.parametrize("cfg", [2, 3])
-def test_fp16x3_mean_strict_bar(cfg):
-    if cfg not in FULL:
-        pytest.skip("needs test_fp16x3_full_size in the same session")
-    mu, rmu = FULL[cfg]
-    assert_close(mu, rmu, what="mu", **REDUCED)
 
 
 def test_replay_matches_suggest():
