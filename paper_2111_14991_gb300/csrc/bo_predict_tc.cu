@@ -24,16 +24,20 @@
 //                quarter of the chunk's observations (packed f32x2, over the
 //                space's own d coordinates), adds its share of k* . alpha,
 //                splits it and stores it in the K-major core-matrix layout.
-//                A row's four quarters sit in one warp and meet by shuffles
-//                to write mu.  The next tile's candidate codes are fetched
-//                while the current tile is computed.
+//                The next tile's candidate codes are fetched while the
+//                current tile is computed.
 //   warps 16-19  drain the accumulator (TMEM lane = row): sum acc_k^2 q_k
-//                (q of the space in shared memory) and write var.  Column block c is final once chunk c's MMAs complete,
-//                so it is drained then (one barrier per block), and each
-//                256-column region is handed back after its last block: the
-//                next tile's first MMAs into a region wait only for that
-//                region.  With n <= 256 the accumulator is double-buffered.
-//   warp 20      issues the MMAs (one thread) and owns the TMEM allocation.
+//                (q of the space in shared memory) and write var; add a
+//                row's four quarter sums of k* . alpha (handed over in shared
+//                memory) and write mu.  A 256-column region is final once the
+//                chunk writing its last column block completes, so it is
+//                drained then and handed back: the next tile's first MMAs into
+//                a region wait only for that region.  With n <= 256 the
+//                accumulator is double-buffered.
+//   warps 20, 22 issue the MMAs (one thread each): warp 20 for accumulator
+//                columns 0-255 (and owns the TMEM allocation), warp 22 for
+//                columns 256-511 when n > 256, so that the two halves'
+//                instruction streams overlap.
 //   warp 21      streams, with bulk copies (one thread), each space's
 //                observation coordinates, 1/s^2 and alpha into shared
 //                memory (double-buffered across spaces) and the L^-1 chunks in pieces of at most 256
@@ -63,7 +67,8 @@ constexpr int kProducerWarps = 16;
 constexpr int kEpiWarp0 = 16;           // warps 16-19
 constexpr int kMmaWarp = 20;
 constexpr int kLoadWarp = 21;
-constexpr int kThreads = 704;
+constexpr int kMmaWarp2 = 22;           // second MMA issuer (columns 256..511)
+constexpr int kThreads = 736;
 constexpr int kPartBytes = kRows * kChunkBytes;   // one split part of an A stage: 8 KB
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 constexpr int kPieceRows = 256;         // rows of L^-1 per B piece (= max MMA N)
@@ -84,6 +89,7 @@ struct TcParams {
   int cw, parts, stages_a;
   int tmem_cols;             // columns of one accumulator buffer
   int acc_stages;            // 1 or 2 accumulator buffers
+  int issuers;               // MMA issuing threads: 2 when some n_pad > 256 (one per 256-column region)
   int xs_bufs;               // 1 or 2 coordinate buffers
   // B (the split L^-1 chunks) in pieces of <= 256 rows: either a ring of
   // b_slots fixed-size slots, or every piece of the space resident (loaded once)
@@ -208,6 +214,16 @@ __device__ __forceinline__ void tc_fence_after() {
 
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// Piece r of chunk c: the L^-1 rows [r0, r0 + wd) of accumulator region r
+// (columns [256 r, 256 r + 256)) that chunk c reaches (rows >= c cw).  The
+// loader and both issuers walk pieces in (chunk, region) order.
+__device__ __forceinline__ bool piece_of(int c, int r, int cw, int n_pad, int* r0, int* wd) {
+  const int lo = max(c * cw, r * kPieceRows), hi = min((r + 1) * kPieceRows, n_pad);
+  *r0 = lo;
+  *wd = hi - lo;
+  return lo < hi;
 }
 
 // K-major, no-swizzle shared-memory matrix descriptor: core matrices of
@@ -437,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
 
   // ---- setup: barriers, TMEM
   if (threadIdx.x == 0) {
-    for (int s = 0; s < SA; ++s) { mbar_init(&a_full[s], kProducerWarps); mbar_init(&a_empty[s], 1); }
+    for (int s = 0; s < SA; ++s) { mbar_init(&a_full[s], kProducerWarps); mbar_init(&a_empty[s], P.issuers); }
     for (int s = 0; s < kMaxBSlots; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
     for (int s = 0; s < kAccBars; ++s) mbar_init(&acc_full[s], 1);
     for (int s = 0; s < 2; ++s) {
@@ -445,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
       mbar_init(&xs_full[s], 1);
       mbar_init(&xs_empty[s], kProducerWarps + 4);   // producers and epilogue warps
     }
-    mbar_init(drain, 1);
+    mbar_init(drain, P.issuers);
     for (int s = 0; s < 2; ++s) {
       mbar_init(&mu_full[s], kProducerWarps);
       mbar_init(&mu_empty[s], 4);
@@ -641,16 +657,23 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         mu = S.mu;
         if (!(ok = mbar_wait(&xs_full[ks % XB], (uint32_t)((ks / XB) & 1), abort_flag, status))) break;
       }
-      // column block c (the chunk's CW columns) is final once chunk c's MMAs
-      // complete: drain it then, and release each 256-column region of the
-      // buffer after its last block
+      // a 256-column region of the accumulator is final once the chunk that
+      // writes its last column block completes (the issuer owning the region
+      // signals that block's barrier): drain the region then and hand it back
       const int as = it % P.acc_stages;
       const uint32_t lane_base = tmem + (uint32_t)(as * P.tmem_cols) + ((uint32_t)(e * 32) << 16);
       uint64_t s2p = 0ull;                       // two columns per packed word
+      // (two issuers, n > 256: every column block is signalled as it becomes
+      // final, so region 0 drains while region 1 is still being accumulated)
+      const bool per_block = P.issuers == 2;
       for (int c = 0; c < chunks && ok; ++c) {
-        if (!(ok = mbar_wait(&acc_full[as * 16 + c], (par[as] >> c) & 1u, abort_flag, status))) break;
-        par[as] ^= 1u << c;
-        tc_fence_after();
+        if (per_block || c == 0) {
+          const int c_end = per_block ? c : min(kPieceRows, n_pad) / CW - 1;
+          if (!(ok = mbar_wait(&acc_full[as * 16 + c_end], (par[as] >> c_end) & 1u, abort_flag, status)))
+            break;
+          par[as] ^= 1u << c_end;
+          tc_fence_after();
+        }
         const int k0 = c * CW;
         float acc[32];
         if constexpr (CW == 16)
@@ -695,16 +718,77 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
       vs_hi = vs_lo = 0.0f;
     }
     vsum = (double)vs_hi + (double)vs_lo;
-  } else if (warp == kMmaWarp) {
-    // ===================== MMA issuer =====================
-    if (lane == 0) {
+  } else if (warp == kMmaWarp || warp == kMmaWarp2) {
+    // ===================== MMA issuers =====================
+    // Issuer r (warp 20: r = 0, warp 22: r = 1) owns accumulator columns
+    // [256 r, 256 r + 256): it issues the B pieces of that region, waits for
+    // the region's drain, and hands over the column blocks it finalises.  Both
+    // wait for every A stage and release it (a_empty counts both).
+    const int r_me = warp == kMmaWarp ? 0 : 1;
+    if (lane == 0 && r_me < P.issuers) {
       const int fmt = MODE == BO_PREC_FP16X3 ? 0 : MODE == BO_PREC_BF16X3 ? 1 : 2;
       const uint32_t a_base = smem_addr(sa), b_base = smem_addr(sb);
-      bool ok = true, issued = false;
+      bool ok = true;
       int it = 0, sa_i = 0, tb = 0, prev = -1, n_pad = 0, chunks = 0;
       uint32_t pha = 0, phb = 0;
-      uint32_t fill[2] = {0u, 0u};  // tiles started per accumulator region
+      uint32_t fill = 0;            // tiles started in this issuer's region (of buffer as)
+      uint32_t fill2[2] = {0u, 0u};
       Work w;
+      if (P.issuers == 1) {
+        // n <= 256 everywhere: one region, one piece per chunk (rows [c cw, n_pad))
+        for (bool more = work_begin(P, w); more && ok; more = work_next(P, w), ++it) {
+          if (w.sess != prev) {
+            prev = w.sess;
+            const TcSess& S = sess_of(P, w.sess);
+            n_pad = S.n_pad;
+            chunks = S.chunks;
+          }
+          const int as = it % P.acc_stages;
+          const uint32_t d_base = tmem + (uint32_t)(as * P.tmem_cols);
+          uint32_t packed = 0;      // resident byte offset of chunk c's piece
+          for (int c = 0; c < chunks && ok; ++c) {
+            const int s = sa_i;
+            if (!(ok = mbar_wait(&a_full[s], pha, abort_flag, status))) break;
+            tc_fence_after();
+            if (c == 0) {           // the buffer's previous tile has been drained
+              if (!(ok = mbar_wait(&acc_empty[as], (fill2[as] & 1u) ^ 1u, abort_flag, status))) break;
+              ++fill2[as];
+              tc_fence_after();
+            }
+            const int r0 = c * cw, wd = n_pad - r0;
+            const uint32_t part_bytes = (uint32_t)((wd >> 3) * 512);
+            const int slot = P.b_resident ? c : tb;
+            if (!(ok = mbar_wait(&b_full[slot], P.b_resident ? 0u : phb, abort_flag, status))) break;
+            tc_fence_after();
+            const uint64_t ad0 = smem_desc(a_base + (uint32_t)(s * parts * kPartBytes), 128, 512);
+            const uint64_t bd0 =
+                smem_desc(b_base + (P.b_resident ? packed : (uint32_t)(tb * P.b_slot_bytes)), 128, 512);
+            const uint32_t idesc = instr_desc(fmt, kRows, wd);
+            const uint32_t dcol = d_base + (uint32_t)r0;
+            const uint32_t first = c > 0 ? 1u : 0u;
+            if (parts == 2) {
+              const uint64_t pbo = (uint64_t)(part_bytes >> 4), pao = (uint64_t)(kPartBytes >> 4);
+              mma<MODE>(dcol, ad0, bd0 + pbo, idesc, first);
+              mma<MODE>(dcol, ad0 + 16, bd0 + pbo + 16, idesc, 1u);
+              mma<MODE>(dcol, ad0 + pao, bd0, idesc, 1u);
+              mma<MODE>(dcol, ad0 + pao + 16, bd0 + 16, idesc, 1u);
+              mma<MODE>(dcol, ad0, bd0, idesc, 1u);
+              mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
+            } else {
+              mma<MODE>(dcol, ad0, bd0, idesc, first);
+              mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
+            }
+            packed += part_bytes * (uint32_t)parts;
+            if (!P.b_resident) {
+              mma_commit(&b_empty[tb]);
+              if (++tb == P.b_slots) { tb = 0; phb ^= 1; }
+            }
+            mma_commit(&a_empty[s]);
+            if (c + 1 == chunks) mma_commit(&acc_full[as * 16 + c]);   // the region is final
+            if (++sa_i == SA) { sa_i = 0; pha ^= 1; }
+          }
+        }
+      } else
       for (bool more = work_begin(P, w); more && ok; more = work_next(P, w), ++it) {
         if (w.sess != prev) {
           prev = w.sess;
@@ -721,52 +805,55 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           if (!(ok = mbar_wait(&a_full[s], pha, abort_flag, status))) break;
           tc_fence_after();
           const uint64_t ad0 = smem_desc(a_base + (uint32_t)(s * parts * kPartBytes), 128, 512);
-          for (int r0 = c * cw; r0 < n_pad && ok; r0 += kPieceRows, ++q) {
-            const int wd = min(kPieceRows, n_pad - r0);         // rows of this piece = MMA N
+          for (int r = 0; r < 2 && ok; ++r) {
+            int r0, wd;
+            if (!piece_of(c, r, cw, n_pad, &r0, &wd)) continue;
             const uint32_t part_bytes = (uint32_t)((wd >> 3) * 512);
-            if (c == 0) {             // first write to this 256-column region since its last drain
-              const int r = as + (r0 >> 8);
-              if (!(ok = mbar_wait(&acc_empty[r], (fill[r] & 1u) ^ 1u, abort_flag, status))) break;
-              ++fill[r];
-              tc_fence_after();
-            }
             const int slot = P.b_resident ? q : tb;
-            if (!(ok = mbar_wait(&b_full[slot], P.b_resident ? 0u : phb, abort_flag, status))) break;
-            tc_fence_after();
             const uint32_t b_st = b_base + (P.b_resident ? packed : (uint32_t)(tb * P.b_slot_bytes));
-            // descriptors advance by address >> 4: +16 is the next 16-element K step
-            const uint64_t bd0 = smem_desc(b_st, 128, 512);
-            const uint32_t idesc = instr_desc(fmt, kRows, wd);
-            const uint32_t dcol = d_base + (uint32_t)r0;
-            const uint32_t first = c > 0 ? 1u : 0u;
-            if (parts == 2) {
-              // products (hi, lo), (lo, hi), (hi, hi): small terms first
-              const uint64_t pbo = (uint64_t)(part_bytes >> 4), pao = (uint64_t)(kPartBytes >> 4);
-              mma<MODE>(dcol, ad0, bd0 + pbo, idesc, first);
-              mma<MODE>(dcol, ad0 + 16, bd0 + pbo + 16, idesc, 1u);
-              mma<MODE>(dcol, ad0 + pao, bd0, idesc, 1u);
-              mma<MODE>(dcol, ad0 + pao + 16, bd0 + 16, idesc, 1u);
-              mma<MODE>(dcol, ad0, bd0, idesc, 1u);
-              mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
-            } else {
-              mma<MODE>(dcol, ad0, bd0, idesc, first);
-              mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
-            }
-            issued = true;
+            ++q;
             packed += part_bytes * (uint32_t)parts;
-            if (!P.b_resident) {
-              mma_commit(&b_empty[tb]);
-              if (++tb == P.b_slots) { tb = 0; phb ^= 1; }
+            const bool mine = r == r_me;
+            if (mine) {
+              if (c == 0) {           // first write to this region since its last drain
+                uint32_t& f = P.acc_stages == 2 ? fill2[as] : fill;
+                if (!(ok = mbar_wait(&acc_empty[as + r], (f & 1u) ^ 1u, abort_flag, status))) break;
+                ++f;
+                tc_fence_after();
+              }
+              if (!(ok = mbar_wait(&b_full[slot], P.b_resident ? 0u : phb, abort_flag, status))) break;
+              tc_fence_after();
+              // descriptors advance by address >> 4: +16 is the next 16-element K step
+              const uint64_t bd0 = smem_desc(b_st, 128, 512);
+              const uint32_t idesc = instr_desc(fmt, kRows, wd);
+              const uint32_t dcol = d_base + (uint32_t)r0;
+              const uint32_t first = c > 0 ? 1u : 0u;
+              if (parts == 2) {
+                // products (hi, lo), (lo, hi), (hi, hi): small terms first
+                const uint64_t pbo = (uint64_t)(part_bytes >> 4), pao = (uint64_t)(kPartBytes >> 4);
+                mma<MODE>(dcol, ad0, bd0 + pbo, idesc, first);
+                mma<MODE>(dcol, ad0 + 16, bd0 + pbo + 16, idesc, 1u);
+                mma<MODE>(dcol, ad0 + pao, bd0, idesc, 1u);
+                mma<MODE>(dcol, ad0 + pao + 16, bd0 + 16, idesc, 1u);
+                mma<MODE>(dcol, ad0, bd0, idesc, 1u);
+                mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
+              } else {
+                mma<MODE>(dcol, ad0, bd0, idesc, first);
+                mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
+              }
+              if (!P.b_resident) mma_commit(&b_empty[tb]);
             }
+            if (!P.b_resident && ++tb == P.b_slots) { tb = 0; phb ^= 1; }
           }
           if (!ok) break;
           mma_commit(&a_empty[s]);
-          mma_commit(&acc_full[as * 16 + c]);  // column block c of this buffer is final
+          if (((c * cw) >> 8) == r_me) mma_commit(&acc_full[as * 16 + c]);  // block c is final
           if (++sa_i == SA) { sa_i = 0; pha ^= 1; }
         }
       }
-      if (issued) {   // every MMA of this CTA has completed before TMEM is released
-        mma_commit(drain);
+      // every MMA of this CTA has completed before TMEM is released (issuer 0 waits for both)
+      mma_commit(drain);
+      if (r_me == 0) {
         unsigned long long t0 = now_ns();
         while (!mbar_test(drain, 0) && now_ns() - t0 < kWaitNs) {
         }
@@ -812,8 +899,9 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         uint32_t packed = 0;
         for (int c = 0; c < chunks && ok; ++c) {
           const size_t goff = (size_t)kChunkBytes * ((size_t)c * n_max - (size_t)ccw * c * (c - 1) / 2);
-          for (int r0 = c * ccw; r0 < n_pad && ok; r0 += kPieceRows, ++q) {
-            const int wd = min(kPieceRows, n_pad - r0);
+          for (int r = 0; r < 2 && ok; ++r) {
+            int r0, wd;
+            if (!piece_of(c, r, ccw, n_pad, &r0, &wd)) continue;
             const uint32_t bytes = (uint32_t)((wd >> 3) * 512);
             const size_t src = goff + (size_t)(r0 - c * ccw) / 8 * 512;
             const int slot = P.b_resident ? q : tb;
@@ -825,6 +913,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
             issued[slot] = 1;
             last_phase[slot] = P.b_resident ? 0 : (int)phb;
             packed += bytes * (uint32_t)parts;
+            ++q;
             if (!P.b_resident && ++tb == P.b_slots) { tb = 0; phb ^= 1; }
           }
         }
@@ -939,6 +1028,7 @@ size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resid
   if (cols > 512) return 0;
   P.tmem_cols = cols;
   P.acc_stages = 2 * cols <= 512 ? 2 : 1;
+  P.issuers = n_pad_max > kPieceRows ? 2 : 1;
   const size_t a_stage = (size_t)P.parts * kPartBytes;
   P.x_buf_bytes = ((size_t)(dmax + 2) * n_pad_max * 4 + 127) / 128 * 128;   // coordinates, 1/s^2, beta/s
   const size_t x_bytes = P.x_buf_bytes * P.xs_bufs;
@@ -946,8 +1036,12 @@ size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resid
   size_t resident = 0;
   int pieces = 0;
   for (int c = 0; c < n_pad_max / P.cw; ++c)
-    for (int r0 = c * P.cw; r0 < n_pad_max; r0 += kPieceRows, ++pieces)
-      resident += (size_t)P.parts * (std::min(kPieceRows, n_pad_max - r0) / 8) * 512;
+    for (int r = 0; r < 2; ++r) {            // the pieces of piece_of(): region r of chunk c
+      const int lo = std::max(c * P.cw, r * kPieceRows), hi = std::min((r + 1) * kPieceRows, n_pad_max);
+      if (lo >= hi) continue;
+      resident += (size_t)P.parts * ((hi - lo) / 8) * 512;
+      ++pieces;
+    }
   P.b_resident = (resident_ok && shape.b_resident >= 0 && pieces <= kMaxBSlots &&
                   resident <= (size_t)P.parts * 64 * 1024) ? 1 : 0;
   P.b_slots = shape.b_slots > 0 ? std::min(shape.b_slots, kMaxBSlots) : 4;
