@@ -1118,15 +1118,22 @@ int launch_predict_tc(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStre
 
 int tc_plan_batch(const TcSess* sess, int count, int dmax, int grid, std::vector<TcSeg>* segs,
                   std::vector<int>* seg_begin) {
-  // estimated cost of one tile of space s: K* production ~ n_pad (dmax + 12)
-  // lane-operations per row, contraction ~ 3 n_pad^2 / 2 MACs at ~32 per lane-op
+  // estimated time of one tile of space s, in microseconds on GB300: a
+  // least-squares fit of per-CTA durations of a 256-space batched pass (1.3 %
+  // residual) to per-tile, per-observation, per-observation-coordinate and
+  // n^2 terms, plus a cost per segment (a space switch)
+  (void)dmax;
+  const double kSwitch = 0.55;
   std::vector<double> tile_cost(count);
   double total = 0.0;
+  int nonempty = 0;
   for (int s = 0; s < count; ++s) {
     const double np = sess[s].n_pad;
-    tile_cost[s] = np * (1.25 * dmax + 12.0) + 3.0 * np * np / 64.0;
+    tile_cost[s] = 1.215 + 0.0272 * np + 3.53e-4 * np * sess[s].d + 1.61e-5 * np * np;
     total += tile_cost[s] * sess[s].num_tiles;
+    nonempty += sess[s].num_tiles > 0;
   }
+  total += kSwitch * (nonempty + grid);    // about one switch per space and per CTA
   segs->clear();
   seg_begin->assign(grid + 1, 0);
   int s = 0, t = 0;
@@ -1145,7 +1152,7 @@ int tc_plan_batch(const TcSess* sess, int count, int dmax, int grid, std::vector
       }
       if (take <= 0) break;
       segs->push_back(TcSeg{s, t, t + take});
-      acc += take * tile_cost[s];
+      acc += take * tile_cost[s] + kSwitch;
       t += take;
       if (t < sess[s].num_tiles) break;
     }
