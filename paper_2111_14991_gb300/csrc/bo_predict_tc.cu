@@ -226,6 +226,15 @@ __device__ __forceinline__ bool piece_of(int c, int r, int cw, int n_pad, int* r
   return lo < hi;
 }
 
+// B slots of accumulator region r's ring: with one issuer a single ring of
+// all slots; with two, the slots split between the regions.
+__host__ __device__ __forceinline__ int ring_size(const TcParams& P, int r) {
+  return P.issuers == 1 ? P.b_slots : (r == 0 ? P.b_slots - P.b_slots / 2 : P.b_slots / 2);
+}
+__host__ __device__ __forceinline__ int ring_base(const TcParams& P, int r) {
+  return r == 0 ? 0 : ring_size(P, 0);
+}
+
 // K-major, no-swizzle shared-memory matrix descriptor: core matrices of
 // 8 rows x 16 bytes, `lbo` bytes apart along K, `sbo` bytes apart along M/N.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -788,7 +797,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
             if (++sa_i == SA) { sa_i = 0; pha ^= 1; }
           }
         }
-      } else
+      } else {
+      const int my_base = ring_base(P, r_me), my_size = ring_size(P, r_me);
       for (bool more = work_begin(P, w); more && ok; more = work_next(P, w), ++it) {
         if (w.sess != prev) {
           prev = w.sess;
@@ -809,8 +819,11 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
             int r0, wd;
             if (!piece_of(c, r, cw, n_pad, &r0, &wd)) continue;
             const uint32_t part_bytes = (uint32_t)((wd >> 3) * 512);
-            const int slot = P.b_resident ? q : tb;
-            const uint32_t b_st = b_base + (P.b_resident ? packed : (uint32_t)(tb * P.b_slot_bytes));
+            // ring mode: region r has its own B ring (slots [ring_base(r), + ring_size(r))),
+            // so each issuer waits only on pieces it consumes (a shared ring would
+            // let an issuer that skips the other's pieces run phases ahead of the loader)
+            const int slot = P.b_resident ? q : my_base + tb;
+            const uint32_t b_st = b_base + (P.b_resident ? packed : (uint32_t)(slot * P.b_slot_bytes));
             ++q;
             packed += part_bytes * (uint32_t)parts;
             const bool mine = r == r_me;
@@ -841,15 +854,18 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
                 mma<MODE>(dcol, ad0, bd0, idesc, first);
                 mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
               }
-              if (!P.b_resident) mma_commit(&b_empty[tb]);
+              if (!P.b_resident) {
+                mma_commit(&b_empty[slot]);
+                if (++tb == my_size) { tb = 0; phb ^= 1; }
+              }
             }
-            if (!P.b_resident && ++tb == P.b_slots) { tb = 0; phb ^= 1; }
           }
           if (!ok) break;
           mma_commit(&a_empty[s]);
           if (((c * cw) >> 8) == r_me) mma_commit(&acc_full[as * 16 + c]);  // block c is final
           if (++sa_i == SA) { sa_i = 0; pha ^= 1; }
         }
+      }
       }
       // every MMA of this CTA has completed before TMEM is released (issuer 0 waits for both)
       mma_commit(drain);
@@ -868,8 +884,9 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
       bool ok = true, b_loaded = false;
       int issued[kMaxBSlots], last_phase[kMaxBSlots], xs_issued[2] = {0, 0}, xs_phase[2] = {0, 0};
       for (int t = 0; t < kMaxBSlots; ++t) issued[t] = last_phase[t] = 0;
-      int tb = 0, ks = -1, prev = -1, n_pad = 0, chunks = 0, n_max = 0;
-      uint32_t phb = 0;
+      int ks = -1, prev = -1, n_pad = 0, chunks = 0, n_max = 0;
+      int rtb[2] = {0, 0};                       // next slot of each region's ring, and its phase
+      uint32_t rph[2] = {0u, 0u};
       const uint8_t* lhi = nullptr;
       const uint8_t* llo = nullptr;
       Work w;
@@ -904,17 +921,17 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
             if (!piece_of(c, r, ccw, n_pad, &r0, &wd)) continue;
             const uint32_t bytes = (uint32_t)((wd >> 3) * 512);
             const size_t src = goff + (size_t)(r0 - c * ccw) / 8 * 512;
-            const int slot = P.b_resident ? q : tb;
-            if (!P.b_resident && !(ok = mbar_wait(&b_empty[tb], phb ^ 1, abort_flag, status))) break;
-            const uint32_t dst = b_base + (P.b_resident ? packed : (uint32_t)(tb * P.b_slot_bytes));
+            const int slot = P.b_resident ? q : ring_base(P, r) + rtb[r];
+            if (!P.b_resident && !(ok = mbar_wait(&b_empty[slot], rph[r] ^ 1u, abort_flag, status))) break;
+            const uint32_t dst = b_base + (P.b_resident ? packed : (uint32_t)(slot * P.b_slot_bytes));
             mbar_arrive_tx(&b_full[slot], bytes * parts);
             bulk_g2s(dst, lhi + src, bytes, &b_full[slot]);
             if (parts == 2) bulk_g2s(dst + bytes, llo + src, bytes, &b_full[slot]);
             issued[slot] = 1;
-            last_phase[slot] = P.b_resident ? 0 : (int)phb;
+            last_phase[slot] = P.b_resident ? 0 : (int)rph[r];
             packed += bytes * (uint32_t)parts;
             ++q;
-            if (!P.b_resident && ++tb == P.b_slots) { tb = 0; phb ^= 1; }
+            if (!P.b_resident && ++rtb[r] == ring_size(P, r)) { rtb[r] = 0; rph[r] ^= 1u; }
           }
         }
         b_loaded = true;
@@ -1045,6 +1062,7 @@ size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resid
   P.b_resident = (resident_ok && shape.b_resident >= 0 && pieces <= kMaxBSlots &&
                   resident <= (size_t)P.parts * 64 * 1024) ? 1 : 0;
   P.b_slots = shape.b_slots > 0 ? std::min(shape.b_slots, kMaxBSlots) : 4;
+  if (P.issuers == 2 && P.b_slots < 2) return 0;   // one ring slot per region at least
   P.b_slot_bytes = (size_t)P.parts * (kPieceRows / 8) * 512;
   const size_t b_bytes = P.b_resident ? resident : P.b_slots * P.b_slot_bytes;
   const size_t fixed = ((b_bytes + 1023) / 1024) * 1024 + ((x_bytes + 1023) / 1024) * 1024 + kMuPartBytes + 512;

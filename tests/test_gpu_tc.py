@@ -179,3 +179,18 @@ def test_autotune_keeps_results():
     mu1, var1 = g.predict()
     assert np.array_equal(mu0, mu1) and np.array_equal(var0, var1)
     g.close()
+
+
+def test_autotune_every_shape_completes_two_issuers():
+    """n > 256 runs two MMA issuers with one B ring per accumulator region:
+    every pipeline shape the autotuner tries must complete without a wait
+    timing out (the status word stays clean) and give the same posterior."""
+    sp = W.config3_space()
+    g, idx, y = state(sp, 300, 6, "fp16x3", n_max=320)
+    mu0, var0 = g.predict()
+    r = g.autotune(reps=1)
+    assert r["tried"] > 4
+    g.sync()                                  # raises on a recorded BO_ERR_TIMEOUT
+    mu1, var1 = g.predict()
+    assert np.array_equal(mu0, mu1) and np.array_equal(var0, var1)
+    g.close()
