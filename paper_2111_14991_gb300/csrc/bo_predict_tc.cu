@@ -298,6 +298,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* r) {
   for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
 }
 
+// Hardware reciprocal square root, flushing subnormals (inputs here are >= 1e-30).
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -360,7 +367,7 @@ template <bool NU52>
 __device__ __forceinline__ uint64_t matern2(uint64_t u2p) {
   float a, b;
   upk2(u2p, a, b);
-  const uint64_t rs = pk2(rsqrtf(a), rsqrtf(b));
+  const uint64_t rs = pk2(rsqrt_approx(a), rsqrt_approx(b));
   const uint64_t u0 = mul2(u2p, rs);
   const uint64_t nu2 = mul2(u2p, dup2(-1.0f));
   const uint64_t hn = mul2(rs, dup2(-0.5f));
@@ -403,22 +410,29 @@ __device__ __forceinline__ void sq_dist(const uint64_t* xcp, uint32_t xrow, int 
   }
 }
 
-// pack two values of the split parts: hi and lo 16-bit words, or one tf32 word
+// Split two K* values (one packed word, element 0 in the low half) into the
+// hi and lo 16-bit words of the FP16X3 / BF16X3 forms: hi = round(k),
+// lo = round(k - hi); each result holds element 0 in its low half.
 template <int MODE>
-__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+__device__ __forceinline__ void split2(uint64_t kv, uint32_t& hi, uint32_t& lo) {
+  float a, b;
+  upk2(kv, a, b);
+  float fa, fb;
   if constexpr (MODE == BO_PREC_FP16X3) {
-    const __half2 h = __floats2half2_rn(a, b);
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
-    hi = *reinterpret_cast<const uint32_t*>(&h);
-    lo = *reinterpret_cast<const uint32_t*>(&l);
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(b), "f"(a));
+    asm("{\n .reg .b16 l, u;\n mov.b32 {l, u}, %2;\n cvt.f32.f16 %0, l;\n cvt.f32.f16 %1, u;\n}\n"
+        : "=f"(fa), "=f"(fb) : "r"(hi));
   } else {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
-    hi = *reinterpret_cast<const uint32_t*>(&h);
-    lo = *reinterpret_cast<const uint32_t*>(&l);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(b), "f"(a));
+    asm("{\n .reg .b16 l, u;\n mov.b32 {l, u}, %2;\n cvt.f32.bf16 %0, l;\n cvt.f32.bf16 %1, u;\n}\n"
+        : "=f"(fa), "=f"(fb) : "r"(hi));
   }
+  float ra, rb;
+  upk2(sub2(kv, pk2(fa, fb)), ra, rb);
+  if constexpr (MODE == BO_PREC_FP16X3)
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(rb), "f"(ra));
+  else
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(rb), "f"(ra));
 }
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
@@ -597,11 +611,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           } else {
             uint32_t h[4], l[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              float ka, kb;
-              upk2(kv[q], ka, kb);
-              split2<MODE>(ka, kb, h[q], l[q]);
-            }
+            for (int q = 0; q < 4; ++q) split2<MODE>(kv[q], h[q], l[q]);
             st_shared_v4(stage, h[0], h[1], h[2], h[3]);
             st_shared_v4(stage + kPartBytes, l[0], l[1], l[2], l[3]);
           }
