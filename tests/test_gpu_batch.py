@@ -103,3 +103,36 @@ def test_batch_rejects_mixed_precision():
         Batch([a, b])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3"])
+def test_batch_with_wide_spaces_equals_alone(precision):
+    """A batch holding a space with n > 256 runs two MMA issuers (one per
+    256-column accumulator region) for every space in it; each space's
+    posterior must still equal its single-space pass, where spaces with
+    n <= 256 take the one-issuer path."""
+    from paper_2111_14991_gb300 import Batch, Space
+    specs = [(21, 9, 30000, 300), (22, 5, 8000, 100), (23, 7, 20000, 260), (24, 4, 2000, 40)]
+    alone, member = [], []
+    for seed, d, n_valid, n0 in specs:
+        sp = W.generic_space(seed, d, n_valid)
+        land = W.Landscape(sp, seed)
+        pair = [Space(sp.grids, sp.invalid, precision=precision, n_max=320) for _ in range(2)]
+        for i in W.clustered_observations(land, n0, seed):
+            v = float(land.clean([i])[0])
+            for s in pair:
+                s.observe(int(i), v)
+        alone.append(pair[0])
+        member.append(pair[1])
+    batch = Batch(member)
+    bidx, bstatus, binfo = batch.suggest()
+    assert not bstatus.any(), bstatus
+    for i, a in enumerate(alone):
+        ai = a.suggest()
+        ma, va = a.last_posterior()
+        mb, vb = member[i].last_posterior()
+        np.testing.assert_array_equal(mb, ma)
+        np.testing.assert_array_equal(vb, va)
+        assert bidx[i] == ai["idx"]
+    for s in alone + member:
+        s.close()
