@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = 1.25
 TRAFFIC = {
     "predict_f64": {"bytes_per_launch": 1088256, "src_sha": "017d135c22181210", "n": 220, "N": 113247,
                     "capture": "profiles/predict_f64_gemm7p_n220.md"},
-    "predict_tc_fp16x3": {"bytes_per_launch": 10373120 + 512, "src_sha": "e891e5add17e1e1c", "n": 512,
+    "predict_tc_fp16x3": {"bytes_per_launch": 10373120 + 256, "src_sha": "2f3709f877634b6e", "n": 512,
                           "N": 1032469, "capture": "profiles/predict_tc_fp16x3_gemm9p_n512.md"},
 }
 
