@@ -49,15 +49,17 @@ struct DevView {
   uint32_t* visited;         // [ceil(N/32)] bit i = configuration i evaluated
 
   double* X;                 // [n_max][d] coordinates of fitted observations
-  float* Xf;                 // [16][n_max] FP32 copy, transposed and scaled as vtab32;
-                             // rows >= d and columns >= n stay zero
+  float* xq;                 // [n_max / 8][ds + 2][8] per group of 8 observations: the FP32
+                             // coordinates scaled as vtab32 (ds rows, rows >= d zero), then
+                             // 1 / s_k^2 of the per-row power-of-two scale s_k of the split
+                             // L^-1 copy, then alpha = L^-T beta (mu = k* . alpha); zero
+                             // beyond n.  Reduced-precision spaces only.
+  int ds;                    // coordinate rows per group: the space's dimension bucket
   double* y;                 // [n_max] raw fitted values
   double* linv;              // [n_max][n_max] L^-1, row-major, lower triangular
   double* beta;              // [n_max] L^-1 y~
   uint8_t* lsplit_hi;        // reduced-precision chunked copy of L^-1 (hi or tf32)
   uint8_t* lsplit_lo;        // (lo part; unused for tf32)
-  float* rowq;               // [n_max] 1 / s_k^2 of the per-row power-of-two scale s_k
-  float* alpha;              // [n_max] alpha = L^-T beta in FP32 (zero beyond n): mu = k* . alpha
 
   void* mu;                  // [N_pad] posterior mean (double for FP64, else float)
   void* var;                 // [N_pad] posterior variance
@@ -75,8 +77,10 @@ struct DevView {
   int max_results;
 };
 
-// Maximum coordinate rows of the transposed FP32 observation copy.
-constexpr int kXfRows = 16;
+// Float index of slot `slot` (coordinate row, ds = 1/s^2, ds + 1 = alpha) of observation j in xq.
+__host__ __device__ inline size_t xq_index(int ds, int j, int slot) {
+  return (size_t)(j >> 3) * (ds + 2) * 8 + (size_t)slot * 8 + (j & 7);
+}
 
 // Scalars of one prediction pass known to the host.
 struct PassArgs {
@@ -113,15 +117,13 @@ struct TcSess {
   const uint8_t* codes;      // [d][N_pad]
   const float* vtab32;       // [d][256] scaled values
   const uint32_t* visited;
-  const float* xf;           // [kXfRows][n_max] scaled observation coordinates
-  const float* rowq;
-  const float* alpha;
+  const float* xq;           // [n_max / 8][ds + 2][8] coordinates, 1/s^2, alpha per 8 observations
   const uint8_t* lhi;        // chunked split copy of L^-1
   const uint8_t* llo;
   float* mu;
   float* var;
   int64_t N, N_pad;
-  int d, n, n_pad, n_max, chunks, num_tiles;
+  int d, ds, n, n_pad, n_max, chunks, num_tiles;
 };
 
 // Tiles [tile0, tile1) of space sess, processed in order by one CTA.

@@ -383,25 +383,26 @@ __device__ __forceinline__ uint64_t matern2(uint64_t u2p) {
 }
 
 // Squared scaled distances of one candidate (xcp: its coordinates, twice per
-// word) to this thread's observations of a chunk (coordinates rows in shared
-// memory at xrow, n_pad floats apart), two observations per packed
-// instruction; accumulators start at 1e-30 so that u^2 > 0.  CHECK: the
-// space has fewer than DMAX coordinates (d, warp-uniform).
+// word) to this thread's observations of a chunk: `grp` is the shared-memory
+// address of their coordinates inside a group of 8 observations (coordinate
+// row p at + 32 p bytes), two observations per packed instruction;
+// accumulators start at 1e-30 so that u^2 > 0.  CHECK: the space has fewer
+// than DMAX coordinates (d, warp-uniform).
 template <int MODE, int DMAX, bool CHECK>
-__device__ __forceinline__ void sq_dist(const uint64_t* xcp, uint32_t xrow, int n_pad, int d, uint64_t* r2p) {
+__device__ __forceinline__ void sq_dist(const uint64_t* xcp, uint32_t grp, int d, uint64_t* r2p) {
   const uint64_t eps = dup2(1e-30f);
   r2p[0] = r2p[1] = r2p[2] = r2p[3] = eps;
 #pragma unroll
   for (int p = 0; p < DMAX; ++p) {
     if (CHECK && p >= d) break;
     uint64_t o0, o1;
-    lds2x64(xrow + (uint32_t)(p * n_pad * 4), o0, o1);
+    lds2x64(grp + (uint32_t)(p * 32), o0, o1);
     uint64_t df = sub2(xcp[p], o0);
     r2p[0] = fma2(df, df, r2p[0]);
     df = sub2(xcp[p], o1);
     r2p[1] = fma2(df, df, r2p[1]);
     if constexpr (MODE != BO_PREC_TF32) {
-      lds2x64(xrow + (uint32_t)(p * n_pad * 4 + 16), o0, o1);
+      lds2x64(grp + (uint32_t)(p * 32 + 16), o0, o1);
       df = sub2(xcp[p], o0);
       r2p[2] = fma2(df, df, r2p[2]);
       df = sub2(xcp[p], o1);
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     bool ok = true;
     int s = 0, ks = -1, prev = -1, tile_it = 0;
     uint32_t ph = 0;                             // ring slot and its phase
-    int n_pad = 0, chunks = 0, d = 0;
+    int n_pad = 0, chunks = 0, d = 0, ds = 0, gstride = 0;
     int64_t N_pad = 0;
     const uint8_t* codes = nullptr;
     const float* vt = nullptr;
@@ -538,6 +539,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         N_pad = S.N_pad;
         codes = S.codes;
         vt = S.vtab32;
+        ds = S.ds;
+        gstride = 32 * (ds + 2);
         xs = xs_base + (uint32_t)((ks % XB) * P.x_buf_bytes);
         if (!(ok = mbar_wait(&xs_full[ks % XB], (uint32_t)((ks / XB) & 1), abort_flag, status))) break;
       }
@@ -575,17 +578,18 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           const int j0 = c * cw + quarter * jq;
           // K* for this thread's observations, computed before waiting for the ring slot
           uint64_t r2p[4];
-          const uint32_t xrow = xs + (uint32_t)(j0 * 4);
+          // this thread's observations inside their group of 8 (coordinates, 1/s^2, alpha)
+          const uint32_t grp = xs + (uint32_t)((j0 >> 3) * gstride + (j0 & 7) * 4);
           if (d == DMAX)
-            sq_dist<MODE, DMAX, false>(xcp, xrow, n_pad, d, r2p);
+            sq_dist<MODE, DMAX, false>(xcp, grp, d, r2p);
           else
-            sq_dist<MODE, DMAX, true>(xcp, xrow, n_pad, d, r2p);
+            sq_dist<MODE, DMAX, true>(xcp, grp, d, r2p);
           uint64_t kv[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q)
             if (2 * q < jq) kv[q] = matern2<NU52>(r2p[q]);
           {
-            const uint32_t arow = xs + (uint32_t)((DMAX + 1) * n_pad * 4 + j0 * 4);
+            const uint32_t arow = grp + (uint32_t)((ds + 1) * 32);
             uint64_t a0, a1;
             lds2x64(arow, a0, a1);
             m2 = fma2(kv[1], a1, fma2(kv[0], a0, m2));
@@ -642,7 +646,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     int n_pad = 0, chunks = 0;
     uint32_t par[2] = {0u, 0u};                  // phase parity of each block barrier, per buffer
     int64_t N = 0;
-    const float* rq = nullptr;                   // 1/s_k^2 of the space, shared memory
+    const float* rq = nullptr;                   // 1/s_k^2 of the space, shared memory (group-strided)
+    int gfloats = 0;                             // floats per group of 8 observations
     const uint32_t* visited = nullptr;
     float* var = nullptr;
     float* mu = nullptr;
@@ -670,7 +675,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         chunks = S.chunks;
         N = S.N;
         const float* xsb = reinterpret_cast<const float*>(smem + P.off_x + (size_t)(ks % XB) * P.x_buf_bytes);
-        rq = xsb + (size_t)DMAX * n_pad;
+        rq = xsb + (size_t)S.ds * 8;             // slot ds of each group of 8 observations
+        gfloats = 8 * (S.ds + 2);
         visited = S.visited;
         var = S.var;
         mu = S.mu;
@@ -701,7 +707,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           tmem_ld32(lane_base + (uint32_t)k0, acc);
 #pragma unroll
         for (int i = 0; i < CW; i += 4) {
-          const float4 q = *reinterpret_cast<const float4*>(rq + k0 + i);
+          const int k = k0 + i;
+          const float4 q = *reinterpret_cast<const float4*>(rq + (k >> 3) * gfloats + (k & 7));
           const uint64_t a01 = pk2(acc[i], acc[i + 1]), a23 = pk2(acc[i + 2], acc[i + 3]);
           s2p = fma2(mul2(a01, pk2(q.x, q.y)), a01, s2p);
           s2p = fma2(mul2(a23, pk2(q.z, q.w)), a23, s2p);
@@ -912,12 +919,9 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           llo = S.llo;
           const int xb = ks % XB;
           if (!(ok = mbar_wait(&xs_empty[xb], (uint32_t)(((ks / XB) & 1) ^ 1), abort_flag, status))) break;
-          const uint32_t row_bytes = (uint32_t)(n_pad * 4);
-          mbar_arrive_tx(&xs_full[xb], row_bytes * (DMAX + 2));
-          const uint32_t dst = xs_base + (uint32_t)(xb * P.x_buf_bytes);
-          for (int p = 0; p < DMAX; ++p) bulk_g2s(dst + (uint32_t)p * row_bytes, S.xf + (size_t)p * n_max, row_bytes, &xs_full[xb]);
-          bulk_g2s(dst + (uint32_t)DMAX * row_bytes, S.rowq, row_bytes, &xs_full[xb]);
-          bulk_g2s(dst + (uint32_t)(DMAX + 1) * row_bytes, S.alpha, row_bytes, &xs_full[xb]);
+          const uint32_t bytes = (uint32_t)(n_pad / 8) * 32u * (uint32_t)(S.ds + 2);
+          mbar_arrive_tx(&xs_full[xb], bytes);
+          bulk_g2s(xs_base + (uint32_t)(xb * P.x_buf_bytes), S.xq, bytes, &xs_full[xb]);
           xs_issued[xb] = 1;
           xs_phase[xb] = (ks / XB) & 1;
         }
@@ -1057,7 +1061,7 @@ size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resid
   P.acc_stages = 2 * cols <= 512 ? 2 : 1;
   P.issuers = n_pad_max > kPieceRows ? 2 : 1;
   const size_t a_stage = (size_t)P.parts * kPartBytes;
-  P.x_buf_bytes = ((size_t)(dmax + 2) * n_pad_max * 4 + 127) / 128 * 128;   // coordinates, 1/s^2, beta/s
+  P.x_buf_bytes = ((size_t)(dmax + 2) * n_pad_max * 4 + 127) / 128 * 128;   // coordinates, 1/s^2, alpha
   const size_t x_bytes = P.x_buf_bytes * P.xs_bufs;
   const size_t limit = 226 * 1024;   // dynamic part; the kernel's static shared memory is small
   size_t resident = 0;
@@ -1107,9 +1111,8 @@ TcSess tc_session(const DevView& v, int n) {
   S.codes = v.codes;
   S.vtab32 = v.vtab32;
   S.visited = v.visited;
-  S.xf = v.Xf;
-  S.rowq = v.rowq;
-  S.alpha = v.alpha;
+  S.xq = v.xq;
+  S.ds = v.ds;
   S.lhi = v.lsplit_hi;
   S.llo = v.lsplit_lo;
   S.mu = static_cast<float*>(v.mu);

@@ -76,8 +76,11 @@ size_t space_device_bytes(int d, int64_t N, int n_max, int precision, int num_sm
   const size_t n = (size_t)((n_max + 31) / 32 * 32);
   const size_t fsz = precision == BO_PREC_FP64 ? 8 : 4;
   size_t t = r(d * N_pad) + r(d * 256 * 8) + r(d * 256 * 4) + r((N_pad / 32 + 1) * 4);
-  t += r(n * d * 8) + r(kXfRows * n * 4) + r(n * 8) + r(n * n * 8) + r(n * 8) + 2 * r(n * 4);
-  if (precision != BO_PREC_FP64) t += (precision == BO_PREC_TF32 ? 1 : 2) * r(lsplit_bytes((int)n, precision));
+  t += r(n * d * 8) + r(n * 8) + r(n * n * 8) + r(n * 8);
+  if (precision != BO_PREC_FP64) {
+    t += r((size_t)(tc_dim_bucket(d) + 2) * n * 4);
+    t += (precision == BO_PREC_TF32 ? 1 : 2) * r(lsplit_bytes((int)n, precision));
+  }
   t += 2 * r(N_pad * fsz) + r((N_pad / 32 + num_sms) * 8) + 2 * r(n * 8) + r(8 * n * 8) + r(sizeof(DevStats));
   t += r((size_t)4 * num_sms * 9 * sizeof(TopEntry)) + r(1024 * sizeof(bo_pass_result));
   return t;
@@ -473,12 +476,11 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   TRY(dalloc_n(s, (size_t)D.d * 256, &vt32));
   TRY(dalloc_n(s, (size_t)N_pad / 32 + 1, &v.visited));
   TRY(dalloc_n(s, (size_t)n_alloc * D.d, &v.X));
-  TRY(dalloc_n(s, (size_t)kXfRows * n_alloc, &v.Xf));
+  v.ds = D.precision == BO_PREC_FP64 ? 0 : tc_dim_bucket(D.d);
+  if (D.precision != BO_PREC_FP64) TRY(dalloc_n(s, (size_t)(v.ds + 2) * n_alloc, &v.xq));
   TRY(dalloc_n(s, (size_t)n_alloc, &v.y));
   TRY(dalloc_n(s, (size_t)n_alloc * n_alloc, &v.linv));
   TRY(dalloc_n(s, (size_t)n_alloc, &v.beta));
-  TRY(dalloc_n(s, (size_t)n_alloc, &v.rowq));
-  TRY(dalloc_n(s, (size_t)n_alloc, &v.alpha));
   if (D.precision != BO_PREC_FP64) {
     TRY(dalloc_n(s, lsplit_bytes(n_alloc, D.precision), &v.lsplit_hi));
     if (D.precision != BO_PREC_TF32) TRY(dalloc_n(s, lsplit_bytes(n_alloc, D.precision), &v.lsplit_lo));

@@ -63,7 +63,7 @@ __device__ __forceinline__ void obs_k_body(const DevView& v, int n, long long id
   if (block == 0 && threadIdx.x < v.d) {
     const double x = coord64(v, idx, threadIdx.x);
     v.X[(size_t)n * v.d + threadIdx.x] = x;
-    v.Xf[(size_t)threadIdx.x * v.n_max + n] = (float)(x * (1.4426950408889634 * c));
+    if (v.xq) v.xq[xq_index(v.ds, n, threadIdx.x)] = (float)(x * (1.4426950408889634 * c));
   }
   if (block == 0 && threadIdx.x == 0) {
     v.y[n] = y_raw;
@@ -186,7 +186,7 @@ __device__ __forceinline__ void obs_finish_body(const DevView& v, int n) {
     int e;
     frexp(m, &e);                       // m in [2^(e-1), 2^e)
     s_scale = ldexpf(1.0f, 14 - e);
-    v.rowq[n] = 1.0f / (s_scale * s_scale);
+    if (v.xq) v.xq[xq_index(v.ds, n, v.ds)] = 1.0f / (s_scale * s_scale);
   }
   __syncthreads();
   const float sc = s_scale;
@@ -241,7 +241,7 @@ __device__ __forceinline__ void obs_alpha_body(const DevView& v, int rows, int b
   double s = 0.0;
   for (int i = col + lane; i < rows; i += 32) s = fma(v.linv[(size_t)i * v.n_max + col], v.beta[i], s);
   s = warp_sum(s);
-  if (lane == 0) v.alpha[col] = (float)s;
+  if (lane == 0) v.xq[xq_index(v.ds, col, v.ds + 1)] = (float)s;
 }
 
 __global__ void obs_beta_kernel(DevView v, int rows, double y_mean, double inv_std) {
