@@ -41,8 +41,9 @@
 //   warp 21      streams, with bulk copies (one thread), each space's
 //                observation coordinates, 1/s^2 and alpha into shared
 //                memory (double-buffered across spaces) and the L^-1 chunks in pieces of at most 256
-//                rows: a 4-slot ring, or, for one space whose pieces fit, all
-//                pieces resident, loaded once.
+//                rows: a ring of slots, or, for one space whose pieces fit, all
+//                pieces resident, loaded once.  With two issuers each region
+//                has its own ring, and warp 23 streams region 1's pieces.
 // K chunk c covers observations j in [c CW, (c+1) CW); only output columns
 // k >= c CW receive it (L^-1 is lower triangular), so the MMA N range
 // shrinks along the chunks.  Every wait is bounded in time: on expiry the
@@ -68,7 +69,8 @@ constexpr int kEpiWarp0 = 16;           // warps 16-19
 constexpr int kMmaWarp = 20;
 constexpr int kLoadWarp = 21;
 constexpr int kMmaWarp2 = 22;           // second MMA issuer (columns 256..511)
-constexpr int kThreads = 736;
+constexpr int kLoadWarp2 = 23;          // loader of the second issuer's L^-1 pieces
+constexpr int kThreads = 768;
 constexpr int kPartBytes = kRows * kChunkBytes;   // one split part of an A stage: 8 KB
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 constexpr int kPieceRows = 256;         // rows of L^-1 per B piece (= max MMA N)
@@ -362,7 +364,9 @@ __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
 // u from the hardware reciprocal square root and one Newton step on the
 // residual u0^2 - u^2, e^-t = 2^-u from the hardware exp2, then (1 + t) e^-t
 // or (1 + t + t^2/3) e^-t.  Everything but the four MUFU operations runs on
-// the packed f32x2 pipe.
+// the packed f32x2 pipe.  (Without the Newton step the sigma error on the
+// 7-parameter space at n = 220 grows from 9e-5 to 2.3e-4, for 2.5 % of the
+// kernel time.)
 template <bool NU52>
 __device__ __forceinline__ uint64_t matern2(uint64_t u2p) {
   float a, b;
@@ -892,9 +896,14 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         }
       }
     }
-  } else if (warp == kLoadWarp) {
+  } else if (warp == kLoadWarp || warp == kLoadWarp2) {
     // ===================== coordinates and L^-1 pieces =====================
-    if (lane == 0) {
+    // Loader 0 copies each space's coordinates in, and the L^-1 pieces of
+    // every region; with two issuers and streamed pieces, loader 1 takes
+    // region 1's ring, so that neither ring waits behind the other.
+    const int l_me = warp == kLoadWarp ? 0 : 1;
+    const bool split = P.issuers == 2 && !P.b_resident;
+    if (lane == 0 && (l_me == 0 || split)) {
       const int eb = MODE == BO_PREC_TF32 ? 4 : 2;
       const int ccw = kChunkBytes / eb;
       const uint32_t b_base = smem_addr(sb);
@@ -917,13 +926,15 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           n_max = S.n_max;
           lhi = S.lhi;
           llo = S.llo;
-          const int xb = ks % XB;
-          if (!(ok = mbar_wait(&xs_empty[xb], (uint32_t)(((ks / XB) & 1) ^ 1), abort_flag, status))) break;
-          const uint32_t bytes = (uint32_t)(n_pad / 8) * 32u * (uint32_t)(S.ds + 2);
-          mbar_arrive_tx(&xs_full[xb], bytes);
-          bulk_g2s(xs_base + (uint32_t)(xb * P.x_buf_bytes), S.xq, bytes, &xs_full[xb]);
-          xs_issued[xb] = 1;
-          xs_phase[xb] = (ks / XB) & 1;
+          if (l_me == 0) {
+            const int xb = ks % XB;
+            if (!(ok = mbar_wait(&xs_empty[xb], (uint32_t)(((ks / XB) & 1) ^ 1), abort_flag, status))) break;
+            const uint32_t bytes = (uint32_t)(n_pad / 8) * 32u * (uint32_t)(S.ds + 2);
+            mbar_arrive_tx(&xs_full[xb], bytes);
+            bulk_g2s(xs_base + (uint32_t)(xb * P.x_buf_bytes), S.xq, bytes, &xs_full[xb]);
+            xs_issued[xb] = 1;
+            xs_phase[xb] = (ks / XB) & 1;
+          }
         }
         if (P.b_resident && b_loaded) continue;  // every piece stays in shared memory
         int q = 0;
@@ -932,6 +943,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           const size_t goff = (size_t)kChunkBytes * ((size_t)c * n_max - (size_t)ccw * c * (c - 1) / 2);
           for (int r = 0; r < 2 && ok; ++r) {
             int r0, wd;
+            if (split && r != l_me) continue;    // the other loader's region
             if (!piece_of(c, r, ccw, n_pad, &r0, &wd)) continue;
             const uint32_t bytes = (uint32_t)((wd >> 3) * 512);
             const size_t src = goff + (size_t)(r0 - c * ccw) / 8 * 512;

@@ -1,6 +1,6 @@
 """A model of the tensor-core prediction kernel's mbarrier protocol (single
 space, the roles of csrc/bo_predict_tc.cu: K* producers, one or two MMA
-issuers, the accumulator epilogue, the bulk-copy loader), run under random
+issuers, the accumulator epilogue, the bulk-copy loaders), run under random
 interleavings.  mbarriers are modelled exactly as the hardware defines them
 (arrival count, phase parity, try_wait on a parity); MMA completion and copy
 landing are immediate.  Every pipeline shape the autotuner tries must finish
@@ -36,7 +36,7 @@ def pieces(c, cw, n_pad):
     return out
 
 
-def run(SA, b_slots, n_pad, shared_ring=False, tiles=4, cw=32, seed=0, max_steps=400_000):
+def run(SA, b_slots, n_pad, shared_ring=False, tiles=4, cw=32, seed=0, max_steps=400_000, split_loaders=True):
     rnd = random.Random(seed)
     chunks = n_pad // cw
     issuers = 2 if n_pad > 256 else 1
@@ -126,15 +126,19 @@ def run(SA, b_slots, n_pad, shared_ring=False, tiles=4, cw=32, seed=0, max_steps
                 yield
             mu_empty[t & 1].arrive()
 
-    def loader():
-        for _, _, slot, ph in slot_seq(None):
+    def loader(region):               # region None: every piece, in chunk order
+        for _, _, slot, ph in slot_seq(region):
             while not b_empty[slot].done(ph ^ 1):
                 yield
             b_full[slot].arrive()
 
-    live = {"producers": producer(), "epilogue": epilogue(), "loader": loader(), "issuer0": issuer(0)}
+    live = {"producers": producer(), "epilogue": epilogue(), "issuer0": issuer(0)}
     if issuers == 2:
         live["issuer1"] = issuer(1)
+    if issuers == 2 and split_loaders and not shared_ring:
+        live["loader0"], live["loader1"] = loader(0), loader(1)   # one loader per region's ring
+    else:
+        live["loader"] = loader(None)
     stalled = 0
     for _ in range(max_steps):
         if not live:
@@ -155,10 +159,11 @@ SHAPES = [(sa, bs) for sa in (2, 3, 4, 6, 8) for bs in (2, 3, 4, 6)]
 
 
 @pytest.mark.parametrize("n_pad", [224, 288, 512])
-def test_every_shape_completes(n_pad):
+@pytest.mark.parametrize("split_loaders", [True, False])
+def test_every_shape_completes(n_pad, split_loaders):
     for sa, bs in SHAPES:
         for seed in range(3):
-            assert run(sa, bs, n_pad, seed=seed) == "ok", (n_pad, sa, bs, seed)
+            assert run(sa, bs, n_pad, seed=seed, split_loaders=split_loaders) == "ok", (n_pad, sa, bs, seed)
 
 
 def test_model_finds_the_shared_ring_deadlock():
