@@ -46,10 +46,14 @@ FP64_PEAK_TFLOPS = 1.25
 # dram bytes per launch of the dominant kernel from an ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (null once the source changes)
 TRAFFIC = {
-    "predict_f64": {"bytes_per_launch": 1088256, "src_sha": "017d135c22181210", "n": 220, "N": 113247,
-                    "capture": "profiles/predict_f64_gemm7p_n220.md"},
-    "predict_tc_fp16x3": {"bytes_per_launch": 10373120 + 256, "src_sha": "2f3709f877634b6e", "n": 512,
-                          "N": 1032469, "capture": "profiles/predict_tc_fp16x3_gemm9p_n512.md"},
+    "predict_f64": [{"bytes_per_launch": 1088256, "src_sha": "017d135c22181210", "n": 220, "N": 113247,
+                     "capture": "profiles/predict_f64_gemm7p_n220.md"}],
+    "predict_tc_fp16x3": [
+        {"bytes_per_launch": 10720768 + 3584, "src_sha": "711b5e50ad39e0af", "n": 512, "N": 1032469,
+         "capture": "profiles/predict_tc_fp16x3_gemm9p_n512.md"},
+        {"bytes_per_launch": 1000704 + 768, "src_sha": "711b5e50ad39e0af", "n": 220, "N": 113247,
+         "capture": "profiles/predict_tc_fp16x3_gemm7p_n220.md"},
+    ],
 }
 
 
@@ -180,9 +184,9 @@ def tc_mma_flops(n, N):
 def traffic_for(key, precision, n, N):
     """Per-launch DRAM bytes from the committed ncu capture of this kernel source
     and launch size, else None."""
-    tr = TRAFFIC.get(key)
-    if tr and tr["src_sha"] == kernel_sha(precision) and tr["n"] == n and tr["N"] == N:
-        return tr["bytes_per_launch"]
+    for tr in TRAFFIC.get(key, []):
+        if tr["src_sha"] == kernel_sha(precision) and tr["n"] == n and tr["N"] == N:
+            return tr["bytes_per_launch"]
     return None
 
 
