@@ -6,7 +6,9 @@
 // 64-column block at a time with register tiling, and reduced on the fly to
 //   var = k(0) - sum_k V_ik^2   (clamped at 0),   mu = sum_k V_ik beta_k,
 // which is the zero-mean GP posterior with beta = L^-1 y~.  Only entries
-// j <= k of L^-1 are non-zero, so each column block stops at its diagonal.
+// j <= k of L^-1 are non-zero, so each column block stops at its diagonal,
+// and inside it each 16-column group skips the slices above its own
+// diagonal and the columns beyond n.
 // Each CTA also writes the sum of the variances of its non-evaluated
 // candidates; the last CTA to finish adds those partial sums in block order
 // (deterministic) into stats->sum_var for the exploration factor (Sec. III-F).
@@ -26,8 +28,45 @@ __device__ __forceinline__ double matern64(double r, double nu, double c) {
   return nu == 1.5 ? (1.0 + t) * e : (1.0 + t + t * t * (1.0 / 3.0)) * e;
 }
 
+// acc[r][q] += K*[row r][j0 + jj] * L^-1[column q][j0 + jj] over the rows
+// jj in [h, h + hn) of a staged slice, for the column groups q in [QLO, QHI)
+// only (compile-time, so that no instruction is spent on the others).
+template <int TM, int QLO, int QHI>
+__device__ __forceinline__ void slice_fma(const double* Ks, const double* Ls, int ldk, int j0, int h, int hn,
+                                          int tx, int ty, double (&acc)[TM][4]) {
+  for (int jj = h; jj < h + hn; ++jj) {
+    double a[TM], b[4];
+#pragma unroll
+    for (int r = 0; r < TM; ++r) a[r] = Ks[(ty + 16 * r) * ldk + j0 + jj];
+#pragma unroll
+    for (int q = QLO; q < QHI; ++q) b[q] = Ls[jj * (kBN + 1) + tx + 16 * q];
+#pragma unroll
+    for (int q = QLO; q < QHI; ++q)
+#pragma unroll
+      for (int r = 0; r < TM; ++r) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+  }
+}
+
+template <int TM>
+__device__ __forceinline__ void slice_groups(int q_lo, int q_hi, const double* Ks, const double* Ls, int ldk,
+                                             int j0, int h, int hn, int tx, int ty, double (&acc)[TM][4]) {
+  switch (q_lo * 8 + q_hi) {
+    case 0 * 8 + 4: slice_fma<TM, 0, 4>(Ks, Ls, ldk, j0, h, hn, tx, ty, acc); break;
+    case 0 * 8 + 3: slice_fma<TM, 0, 3>(Ks, Ls, ldk, j0, h, hn, tx, ty, acc); break;
+    case 0 * 8 + 2: slice_fma<TM, 0, 2>(Ks, Ls, ldk, j0, h, hn, tx, ty, acc); break;
+    case 0 * 8 + 1: slice_fma<TM, 0, 1>(Ks, Ls, ldk, j0, h, hn, tx, ty, acc); break;
+    case 1 * 8 + 4: slice_fma<TM, 1, 4>(Ks, Ls, ldk, j0, h, hn, tx, ty, acc); break;
+    case 1 * 8 + 3: slice_fma<TM, 1, 3>(Ks, Ls, ldk, j0, h, hn, tx, ty, acc); break;
+    case 1 * 8 + 2: slice_fma<TM, 1, 2>(Ks, Ls, ldk, j0, h, hn, tx, ty, acc); break;
+    case 2 * 8 + 4: slice_fma<TM, 2, 4>(Ks, Ls, ldk, j0, h, hn, tx, ty, acc); break;
+    case 2 * 8 + 3: slice_fma<TM, 2, 3>(Ks, Ls, ldk, j0, h, hn, tx, ty, acc); break;
+    case 3 * 8 + 4: slice_fma<TM, 3, 4>(Ks, Ls, ldk, j0, h, hn, tx, ty, acc); break;
+    default: break;   // q_lo >= q_hi: nothing in this half
+  }
+}
+
 template <int BM>
-__global__ void __launch_bounds__(kThreads) predict_f64_kernel(DevView v, int n, int n_pad) {
+__global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int n, int n_pad) {
   constexpr int TM = BM / 16;             // rows per thread
   extern __shared__ double smem[];
   const int d = v.d;
@@ -83,6 +122,9 @@ __global__ void __launch_bounds__(kThreads) predict_f64_kernel(DevView v, int n,
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[r][q] = 0.0;
     const int jend = min(n, kb + kBN);      // L^-1[k][j] = 0 for j > k
+    // column group q (columns kb + 16q .. kb + 16q + 15) holds real columns
+    // only below n: groups from q_hi on are never touched
+    const int q_hi = min(4, (n - kb + 15) / 16);
     for (int j0 = 0; j0 < jend; j0 += kBK) {
       __syncthreads();
       for (int e = tid; e < kBN * kBK; e += kThreads) {
@@ -92,16 +134,13 @@ __global__ void __launch_bounds__(kThreads) predict_f64_kernel(DevView v, int n,
       }
       __syncthreads();
       const int jn = min(kBK, jend - j0);
-      for (int jj = 0; jj < jn; ++jj) {
-        double a[TM], b[4];
-#pragma unroll
-        for (int r = 0; r < TM; ++r) a[r] = Ks[(ty + 16 * r) * ldk + j0 + jj];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) b[q] = Ls[jj * (kBN + 1) + tx + 16 * q];
-#pragma unroll
-        for (int r = 0; r < TM; ++r)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+      // in 16-row halves of the slice: groups whose last column lies before
+      // the half's first row j meet only zeros of L^-1 there (the triangle
+      // inside the diagonal block); (q_lo, q_hi) is uniform across the CTA,
+      // and the skipped products are exact zeros
+      for (int h = 0; h < jn; h += 16) {
+        const int j = j0 + h, q_lo = j > kb + 15 ? (j - kb) / 16 : 0;
+        slice_groups<TM>(q_lo, q_hi, Ks, Ls, ldk, j0, h, min(16, jn - h), tx, ty, acc);
       }
     }
 #pragma unroll
