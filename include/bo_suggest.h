@@ -149,7 +149,9 @@ typedef struct bo_space bo_space;   /* opaque, owned by the library */
 
 /* Build the valid list, upload codes and value tables, and allocate the
  * resident state (observations, L^-1, beta, per-candidate buffers) for
- * n_max observations.  Synchronous. */
+ * n_max observations.  Synchronous.  BO_ERR_ARG for a bad descriptor, a
+ * Cartesian product above 2^40 configurations, or (reduced precision) 2^32 - 1
+ * or more valid configurations. */
 int bo_space_create(const bo_space_desc* desc, bo_space** out);
 /* Release every resource of the space (synchronizes its stream). */
 int bo_space_destroy(bo_space* space);

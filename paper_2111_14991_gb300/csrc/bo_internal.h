@@ -196,7 +196,10 @@ void tc_force_shape(const TcShape* shape);
 void tc_store_shape(int precision, int dmax, int n_pad, bool batched, const TcShape& shape);
 int launch_acquire(const DevView& v, const PassArgs& a, cudaStream_t s);
 int launch_acquire(const AcqDev& v, const PassArgs& a, bool f64, cudaStream_t s);
-int acquire_grid(int64_t n_cand, int max_blocks);
+// Blocks of an acquisition pass over n_cand candidates, per_thread candidates
+// per thread (a single space: few, so that the pass fills the GPU; a batch of
+// spaces: many, the spaces together fill it), at most max_blocks.
+int acquire_grid(int64_t n_cand, int max_blocks, int per_thread = 16);
 int launch_acquire_batch(const AcqItem* items, const int* block_item, const int* block_local,
                          const double* seg_part, int total_blocks, bool f64, cudaStream_t s);
 

@@ -426,6 +426,11 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   int64_t nvalid = 0;
   for (int64_t f = 0; f < total; ++f) nvalid += !(D.invalid_mask && D.invalid_mask[f]);
   if (nvalid == 0) { delete s; return fail(BO_ERR_ARG, "no valid configuration"); }
+  // the FP32 acquisition packs a valid-list index into 32 bits
+  if (D.precision != BO_PREC_FP64 && nvalid >= (int64_t)0xFFFFFFFF) {
+    delete s;
+    return fail(BO_ERR_ARG, "reduced precision holds fewer than 2^32 - 1 valid configurations");
+  }
   s->N = nvalid;
   const int64_t N_pad = (nvalid + kTileRows - 1) / kTileRows * kTileRows;
   std::vector<uint8_t> codes((size_t)D.d * N_pad, 0);
