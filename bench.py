@@ -46,7 +46,7 @@ FP64_PEAK_TFLOPS = 1.25
 # dram bytes per launch of the dominant kernel from an ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (null once the source changes)
 TRAFFIC = {
-    "predict_f64": [{"bytes_per_launch": 1088256, "src_sha": "017d135c22181210", "n": 220, "N": 113247,
+    "predict_f64": [{"bytes_per_launch": 1121024, "src_sha": "b7fa0aef9ab9f7cf", "n": 220, "N": 113247,
                      "capture": "profiles/predict_f64_gemm7p_n220.md"}],
     "predict_tc_fp16x3": [
         {"bytes_per_launch": 10720768 + 3584, "src_sha": "711b5e50ad39e0af", "n": 512, "N": 1032469,
@@ -197,7 +197,7 @@ def roofline_for(precision, n, d, N, k1_time):
         ach = fl / k1_time / 1e12
         return {"bound": "alu", "kernel": "predict_f64_kernel", "achieved": round(ach, 4),
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "nominal GB300 FP64 (recipe table), not measured; ncu: FP64 pipe 94.5 % busy",
+                "peak_source": "nominal GB300 FP64 (recipe table), not measured; ncu: FP64 pipe 93 % busy",
                 "traffic": traffic_for("predict_f64", precision, n, N),
                 "flops_per_launch": fl, "launch_s": k1_time}
     peaks = _peaks()
