@@ -27,6 +27,10 @@ struct DevStats {
   unsigned int k2_done;
   int32_t status;            // sticky BO_ERR_* of observation updates
   int32_t pad;
+  unsigned int coop_count;   // grid-barrier arrivals of the fused update (reset by its last block)
+  unsigned int coop_done;    // blocks that left the fused update
+  int32_t coop_abort;        // a grid-barrier wait of the fused update timed out
+  int32_t pad2;
 };
 
 struct TopEntry {

@@ -9,6 +9,8 @@
 // full because the standardization of y shifts with every observation.
 // The reduced-precision contraction gets a per-row scaled, split copy of each
 // new row (written once), see lsplit_offset().
+#include <algorithm>
+
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -341,9 +343,121 @@ int launch_set_visited(const DevView& v, int64_t idx, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
+// ---- the whole update of one space in one cooperative launch ----------------
+// The phases above run as virtual blocks of 256 threads over a co-resident
+// grid, separated by grid barriers (arrival counter in DevStats, bounded wait:
+// on expiry the update records BO_ERR_TIMEOUT and every block leaves).  One
+// launch instead of six saves the launch gaps that dominate at small n.
+constexpr int kFusedThreads = 256;
+constexpr unsigned long long kCoopWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long coop_now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Arrive at grid barrier number `phase` (1, 2, ...) and wait for every block.
+__device__ __forceinline__ bool coop_sync(DevStats* st, unsigned int phase) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&st->coop_count, 1u);
+    const unsigned int target = phase * gridDim.x;
+    const unsigned long long t0 = coop_now_ns();
+    while (*(volatile unsigned int*)&st->coop_count < target) {
+      if (*(volatile int32_t*)&st->coop_abort) break;
+      if (coop_now_ns() - t0 > kCoopWaitNs) {
+        atomicExch(&st->coop_abort, 1);
+        atomicExch(&st->status, BO_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int32_t*)&st->coop_abort == 0;
+}
+
+__global__ void __launch_bounds__(kFusedThreads) obs_fused_kernel(DevView v, int n, long long idx, double y_raw,
+                                                                  double y_mean, double inv_std) {
+  DevStats* st = v.stats;
+  const int G = (int)gridDim.x;
+  const int rows = n + 1;
+  unsigned int phase = 0;
+  do {
+    for (int b = blockIdx.x; b < (n + kFusedThreads - 1) / kFusedThreads + (n == 0); b += G)
+      obs_k_body(v, n, idx, y_raw, b);
+    if (n > 0) {
+      if (!coop_sync(st, ++phase)) break;
+      for (int b = blockIdx.x; b < (n + 7) / 8; b += G) obs_l_body(v, n, b);
+      if (!coop_sync(st, ++phase)) break;
+      const int gx = (n + 31) / 32, gy = (n + 63) / 64;
+      for (int b = blockIdx.x; b < gx * gy; b += G) {
+        obs_w_body(v, n, b % gx, b / gx);
+        __syncthreads();                       // its shared partials are reused by the next one
+      }
+    }
+    if (!coop_sync(st, ++phase)) break;
+    if (blockIdx.x == 0) obs_finish_body(v, n);
+    if (!coop_sync(st, ++phase)) break;
+    for (int b = blockIdx.x; b < (rows + 7) / 8; b += G) obs_beta_body(v, rows, y_mean, inv_std, b);
+    if (v.precision != BO_PREC_FP64) {
+      if (!coop_sync(st, ++phase)) break;
+      for (int b = blockIdx.x; b < (rows + 7) / 8; b += G) obs_alpha_body(v, rows, b);
+    }
+  } while (false);
+  // the last block to leave resets the barrier state for the next update
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&st->coop_done, 1u) == (unsigned int)G - 1) {
+      st->coop_count = 0;
+      st->coop_abort = 0;
+      st->coop_done = 0;
+      __threadfence();
+    }
+  }
+}
+
+// Blocks of the fused update for n fitted observations: the largest phase,
+// capped by what is co-resident (-1 if the occupancy query fails).
+int fused_update_grid(int n) {
+  static int max_blocks = 0;
+  if (max_blocks == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, obs_fused_kernel, kFusedThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      return -1;
+    max_blocks = sms * per_sm;
+  }
+  const int rows = n + 1;
+  int want = std::max(1, (n + kFusedThreads - 1) / kFusedThreads);
+  want = std::max(want, (n + 7) / 8);
+  want = std::max(want, ((n + 31) / 32) * ((n + 63) / 64));
+  want = std::max(want, (rows + 7) / 8);
+  return std::min(want, max_blocks);
+}
+
 int launch_observe_update(const DevView& v, int n, int64_t idx, double y_raw, double y_mean,
                           double y_std, cudaStream_t s) {
   // n = observations fitted before this one; the new one becomes row n.
+  {
+    const int grid = fused_update_grid(n);
+    if (grid > 0) {
+      long long idx_ll = (long long)idx;
+      double inv_std = 1.0 / y_std;
+      DevView vv = v;
+      void* args[] = {&vv, &n, &idx_ll, &y_raw, &y_mean, &inv_std};
+      if (cudaLaunchCooperativeKernel((const void*)obs_fused_kernel, dim3(grid), dim3(kFusedThreads), args, 0, s) ==
+          cudaSuccess)
+        return 1;
+      (void)cudaGetLastError();   // not launchable cooperatively here: the phase kernels below
+    }
+  }
   int launches = 0;
   obs_k_kernel<<<(n + 31) / 32 + (n == 0), 32, 0, s>>>(v, n, (long long)idx, y_raw);
   ++launches;
