@@ -378,6 +378,19 @@ typedef struct bo_acq_params {
 int bo_acquire_noalloc(const void* mu, const void* var, const uint32_t* visited, int32_t f64,
                        const bo_acq_params* params, bo_pass_result* result, void* stream);
 
+/* ---- self-test of the bounded device waits ------------------------------ */
+/* Every wait inside this library's kernels (mbarrier phases of the prediction
+ * kernel, grid barriers of the fused observation update) gives up after 2 s,
+ * records BO_ERR_TIMEOUT and lets the kernel return, so that a stuck pipeline
+ * surfaces as an error and the CUDA context stays usable.  This entry point
+ * makes one wait of each kind run out on purpose (a barrier phase that nothing
+ * completes; a grid barrier that one of two blocks never reaches) on the
+ * current device and reports what each recorded: BO_ERR_TIMEOUT when the
+ * mechanism works.  Takes about 4 s; allocates and frees 64 bytes of device
+ * memory; synchronous.  Returns BO_ERR_ARG for null outputs, BO_ERR_CUDA if a
+ * launch or copy fails. */
+int bo_selftest_waits(int32_t* mbar_status, int32_t* grid_status);
+
 /* Number of kernel launches this library has issued on the space so far. */
 int bo_launch_count(const bo_space* space, int64_t* out);
 

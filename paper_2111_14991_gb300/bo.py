@@ -130,6 +130,7 @@ SIGNATURES = {
     "bo_replay_enqueue": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "bo_replay_fetch": (C.c_int, [C.c_void_p, C.POINTER(PassResult), C.c_int32]),
     "bo_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "bo_selftest_waits": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "bo_acquire_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                      C.POINTER(AcqParams), C.c_void_p, C.c_void_p]),
     "bo_last_error": (C.c_char_p, []),
@@ -449,6 +450,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def selftest_waits():
+    """bo_selftest_waits: (mbarrier wait status, grid barrier status), each
+    BO_ERR_TIMEOUT when the bounded waits work (see include/bo_suggest.h)."""
+    a, b = C.c_int32(), C.c_int32()
+    _check(lib().bo_selftest_waits(C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def acquire_noalloc(mu_ptr, var_ptr, visited_ptr, f64, params, result_ptr, stream_ptr):

@@ -1118,6 +1118,22 @@ int num_sms() {
 
 }  // namespace
 
+// Self-test of the bounded mbarrier wait every role of the prediction kernel
+// uses: one thread waits for a phase that nothing completes; the wait gives up
+// after its limit, raises the abort flag and records BO_ERR_TIMEOUT.
+__global__ void selftest_mbar_kernel(int32_t* status, int* abort_flag) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);                  // count 1, and no thread ever arrives
+    (void)mbar_wait(&bar, 0, abort_flag, status);
+  }
+}
+
+int launch_selftest_mbar(int32_t* status, int* abort_flag, cudaStream_t s) {
+  selftest_mbar_kernel<<<1, 32, 0, s>>>(status, abort_flag);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
 TcSess tc_session(const DevView& v, int n) {
   TcSess S{};
   S.codes = v.codes;

@@ -701,6 +701,29 @@ int bo_replay_fetch(bo_space* s, bo_pass_result* out, int32_t steps) {
   return BO_OK;
 }
 
+int bo_selftest_waits(int32_t* mbar_status, int32_t* grid_status) {
+  if (!mbar_status || !grid_status) return fail(BO_ERR_ARG, "null argument");
+  // [0, 8): mbarrier status, [8, 16): its abort flag, [16, 16 + sizeof(DevStats)): grid barrier state
+  static_assert(16 + sizeof(DevStats) <= 64, "scratch size");
+  void* buf = nullptr;
+  BO_CUDA(cudaMalloc(&buf, 64));
+  cudaError_t e = cudaMemset(buf, 0, 64);
+  auto* bytes = static_cast<uint8_t*>(buf);
+  int32_t* st1 = reinterpret_cast<int32_t*>(bytes);
+  int* abort1 = reinterpret_cast<int*>(bytes + 8);
+  DevStats* st2 = reinterpret_cast<DevStats*>(bytes + 16);
+  if (e == cudaSuccess && launch_selftest_mbar(st1, abort1, nullptr) < 0) e = cudaGetLastError();
+  if (e == cudaSuccess && launch_selftest_grid(st2, nullptr) < 0) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  DevStats h2{};
+  if (e == cudaSuccess) e = cudaMemcpy(mbar_status, st1, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&h2, st2, sizeof h2, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "self-test of the bounded waits");
+  *grid_status = h2.status;
+  return BO_OK;
+}
+
 int bo_launch_count(const bo_space* s, int64_t* out) {
   if (!s || !out) return fail(BO_ERR_ARG, "null argument");
   *out = s->launches;

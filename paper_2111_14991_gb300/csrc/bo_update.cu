@@ -421,6 +421,20 @@ __global__ void __launch_bounds__(kFusedThreads) obs_fused_kernel(DevView v, int
   }
 }
 
+// Self-test of the fused update's grid barrier: block 1 of two never arrives,
+// so block 0's bounded wait runs out and records BO_ERR_TIMEOUT in st.
+__global__ void selftest_grid_kernel(DevStats* st) {
+  if (blockIdx.x == 0) (void)coop_sync(st, 1);
+}
+
+int launch_selftest_grid(DevStats* st, cudaStream_t s) {
+  void* args[] = {&st};
+  return cudaLaunchCooperativeKernel((const void*)selftest_grid_kernel, dim3(2), dim3(kFusedThreads), args, 0, s) ==
+                 cudaSuccess
+             ? 1
+             : -1;
+}
+
 // Blocks of the fused update for n fitted observations: the largest phase,
 // capped by what is co-resident (-1 if the occupancy query fails).
 int fused_update_grid(int n) {
