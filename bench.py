@@ -49,9 +49,9 @@ TRAFFIC = {
     "predict_f64": [{"bytes_per_launch": 1121024, "src_sha": "b7fa0aef9ab9f7cf", "n": 220, "N": 113247,
                      "capture": "profiles/predict_f64_gemm7p_n220.md"}],
     "predict_tc_fp16x3": [
-        {"bytes_per_launch": 10720768 + 3584, "src_sha": "711b5e50ad39e0af", "n": 512, "N": 1032469,
+        {"bytes_per_launch": 10721536 + 4352, "src_sha": "2ae31266fefb7a2f", "n": 512, "N": 1032469,
          "capture": "profiles/predict_tc_fp16x3_gemm9p_n512.md"},
-        {"bytes_per_launch": 1000704 + 768, "src_sha": "711b5e50ad39e0af", "n": 220, "N": 113247,
+        {"bytes_per_launch": 1005056 + 0, "src_sha": "2ae31266fefb7a2f", "n": 220, "N": 113247,
          "capture": "profiles/predict_tc_fp16x3_gemm7p_n220.md"},
     ],
 }
