@@ -181,7 +181,7 @@ struct VisitItem {
 // Self-tests of the bounded device waits (each returns 1 when launched).
 int launch_selftest_mbar(int32_t* status, int* abort_flag, cudaStream_t s);
 int launch_selftest_grid(DevStats* st, cudaStream_t s);
-int launch_observe_update(const DevView& v, int n, int64_t idx, double y_raw, double y_mean,
+int launch_observe_update(bool cooperative, const DevView& v, int n, int64_t idx, double y_raw, double y_mean,
                           double y_std, cudaStream_t s);
 int launch_set_visited(const DevView& v, int64_t idx, cudaStream_t s);
 // Block tables of the batched update phases k, l, w, beta (concatenated) for spaces with

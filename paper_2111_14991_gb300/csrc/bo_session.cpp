@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -248,7 +249,7 @@ int observe_impl(bo_space* s, int64_t idx, double value) {
   double mean = 0.0, sd = 1.0;
   int rc = observe_host(s, idx, value, &fit, &n_before, &mean, &sd);
   if (rc != BO_OK) return rc;
-  const int k = fit ? launch_observe_update(s->v, n_before, idx, value, mean, sd, s->stream)
+  const int k = fit ? launch_observe_update(s->coop_update, s->v, n_before, idx, value, mean, sd, s->stream)
                     : launch_set_visited(s->v, idx, s->stream);
   if (k < 0) return fail(BO_ERR_CUDA, "update launch failed");
   s->launches += k;
@@ -417,6 +418,7 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   s->d = D.d;
   s->n_cap = D.n_max;
   s->rng = D.seed;
+  s->coop_update = getenv("BO_NO_COOP") == nullptr;
   s->sel.init(D.af, D.skip_threshold, D.discount, D.rif);
   for (int p = 0; p < D.d; ++p) {
     s->sizes.push_back(D.n_values[p]);

@@ -177,6 +177,7 @@ struct bo_space {
   int64_t launches = 0;
   int replay_steps = 0;
   int poisoned = BO_OK;
+  bool coop_update = true;           // one cooperative launch per observation update
 };
 
 namespace bo {

@@ -456,10 +456,10 @@ int fused_update_grid(int n) {
   return std::min(want, max_blocks);
 }
 
-int launch_observe_update(const DevView& v, int n, int64_t idx, double y_raw, double y_mean,
+int launch_observe_update(bool cooperative, const DevView& v, int n, int64_t idx, double y_raw, double y_mean,
                           double y_std, cudaStream_t s) {
   // n = observations fitted before this one; the new one becomes row n.
-  {
+  if (cooperative) {
     const int grid = fused_update_grid(n);
     if (grid > 0) {
       long long idx_ll = (long long)idx;
