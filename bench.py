@@ -46,12 +46,12 @@ FP64_PEAK_TFLOPS = 1.25
 # dram bytes per launch of the dominant kernel from an ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (null once the source changes)
 TRAFFIC = {
-    "predict_f64": [{"bytes_per_launch": 1121024, "src_sha": "b7fa0aef9ab9f7cf", "n": 220, "N": 113247,
+    "predict_f64": [{"bytes_per_launch": 1419776 + 0, "src_sha": "67487f6f85df9915", "n": 220, "N": 113247,
                      "capture": "profiles/predict_f64_gemm7p_n220.md"}],
     "predict_tc_fp16x3": [
-        {"bytes_per_launch": 10721536 + 4352, "src_sha": "2ae31266fefb7a2f", "n": 512, "N": 1032469,
+        {"bytes_per_launch": 10716672 + 3584, "src_sha": "881cb10161712188", "n": 512, "N": 1032469,
          "capture": "profiles/predict_tc_fp16x3_gemm9p_n512.md"},
-        {"bytes_per_launch": 1005056 + 0, "src_sha": "2ae31266fefb7a2f", "n": 220, "N": 113247,
+        {"bytes_per_launch": 1005568 + 0, "src_sha": "881cb10161712188", "n": 220, "N": 113247,
          "capture": "profiles/predict_tc_fp16x3_gemm7p_n220.md"},
     ],
 }

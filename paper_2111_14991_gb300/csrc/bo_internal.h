@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -84,6 +85,26 @@ struct DevView {
 // Float index of slot `slot` (coordinate row, ds = 1/s^2, ds + 1 = alpha) of observation j in xq.
 __host__ __device__ inline size_t xq_index(int ds, int j, int slot) {
   return (size_t)(j >> 3) * (ds + 2) * 8 + (size_t)slot * 8 + (j & 7);
+}
+
+// Per-device launch attributes, set once and shared by every host thread:
+// raise `kernel`'s dynamic shared-memory limit on the current device to at
+// least `bytes` (configured[] remembers each device's value; one lock orders
+// concurrent callers, so a smaller request never lowers a larger limit).
+constexpr int kMaxDevices = 64;
+inline std::mutex& launch_attr_mutex() {
+  static std::mutex m;
+  return m;
+}
+inline bool ensure_dynamic_smem(const void* kernel, size_t (&configured)[kMaxDevices], size_t bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+  std::lock_guard<std::mutex> lk(launch_attr_mutex());
+  if (configured[dev] >= bytes) return true;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    return false;
+  configured[dev] = bytes;
+  return true;
 }
 
 // Scalars of one prediction pass known to the host.

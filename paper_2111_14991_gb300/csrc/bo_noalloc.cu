@@ -30,7 +30,6 @@ static_assert((int64_t)kNoallocBlocks * kCandPerBlock == BO_NOALLOC_MAX_CAND, "d
 
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
 
-constexpr int kMaxDevices = 64;
 std::mutex g_lookup_mu;
 NoallocScratch* g_scratch_addr[kMaxDevices] = {};
 

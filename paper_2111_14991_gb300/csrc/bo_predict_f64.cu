@@ -205,13 +205,8 @@ template <int BM>
 int launch_bm(const DevView& v, int n, cudaStream_t s) {
   const int n_pad = ((n + kBK - 1) / kBK) * kBK;
   const size_t sm = smem_bytes<BM>(v.d, n_pad);
-  static int configured = 0;
-  if (configured < (int)sm) {
-    if (cudaFuncSetAttribute(predict_f64_kernel<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm) != cudaSuccess)
-      return -1;
-    configured = (int)sm;
-  }
+  static size_t configured[kMaxDevices] = {};
+  if (!ensure_dynamic_smem((const void*)predict_f64_kernel<BM>, configured, sm)) return -1;
   const int grid = (int)(v.N_pad / BM);
   if (grid > v.max_partials) return -1;
   predict_f64_kernel<BM><<<grid, kThreads, sm, s>>>(v, n, n_pad);

@@ -1022,13 +1022,8 @@ TcShape shape_for(int precision, int dmax, int n_pad, bool batched) {
 
 template <int MODE, int DMAX, bool NU52>
 int launch_mode(const TcParams& P, size_t smem, int grid, cudaStream_t s) {
-  static size_t configured = 0;
-  if (configured < smem) {
-    if (cudaFuncSetAttribute(predict_tc_kernel<MODE, DMAX, NU52>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return -1;
-    configured = smem;
-  }
+  static size_t configured[kMaxDevices] = {};
+  if (!ensure_dynamic_smem((const void*)predict_tc_kernel<MODE, DMAX, NU52>, configured, smem)) return -1;
   predict_tc_kernel<MODE, DMAX, NU52><<<grid, kThreads, smem, s>>>(P);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }

@@ -436,17 +436,25 @@ int launch_selftest_grid(DevStats* st, cudaStream_t s) {
 }
 
 // Blocks of the fused update for n fitted observations: the largest phase,
-// capped by what is co-resident (-1 if the occupancy query fails).
+// capped by what is co-resident on the current device (-1 if the occupancy
+// query fails).
 int fused_update_grid(int n) {
-  static int max_blocks = 0;
-  if (max_blocks == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, obs_fused_kernel, kFusedThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-      return -1;
-    max_blocks = sms * per_sm;
+  static int co_resident[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+  int max_blocks;
+  {
+    std::lock_guard<std::mutex> lk(launch_attr_mutex());
+    if (co_resident[dev] == 0) {
+      int sms = 0, per_sm = 0;
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, obs_fused_kernel, kFusedThreads, 0) !=
+              cudaSuccess ||
+          per_sm < 1)
+        return -1;
+      co_resident[dev] = sms * per_sm;
+    }
+    max_blocks = co_resident[dev];
   }
   const int rows = n + 1;
   int want = std::max(1, (n + kFusedThreads - 1) / kFusedThreads);
