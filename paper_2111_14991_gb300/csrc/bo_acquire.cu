@@ -85,20 +85,27 @@ struct Math<double> {
   __device__ static double sqrt_(double x) { return sqrt(x); }
 };
 
-// score of acquisition function af at posterior (mu, sigma); larger is better
+// the three scores at posterior (mu, sigma), larger is better: EI and PI share
+// z and Phi (evaluated only when need_phi: EI or PI is active), LCB is
+// -(mu - lam sigma)
 template <typename T>
-__device__ __forceinline__ T score(int af, T mu, T sigma, T fplus, T lam) {
+__device__ __forceinline__ void scores3(T mu, T sigma, T fplus, T lam, bool need_phi, T& ei, T& pi, T& lcb) {
   const T delta = fplus - mu - lam;
-  if (af == kLCB) return lam * sigma - mu;
+  lcb = lam * sigma - mu;
+  if (!need_phi) {
+    ei = pi = T(0);
+    return;
+  }
   if (!(sigma > T(0))) {
-    if (af == kEI) return delta > T(0) ? delta : T(0);
-    return delta > T(0) ? T(1) : T(0);
+    ei = delta > T(0) ? delta : T(0);
+    pi = delta > T(0) ? T(1) : T(0);
+    return;
   }
   const T z = delta / sigma;
   const T Phi = T(0.5) * Math<T>::erfc_(-z * T(0.70710678118654752440));
-  if (af == kPI) return Phi;
   const T phi = Math<T>::exp_(T(-0.5) * z * z) * T(0.39894228040143267794);
-  return delta * Phi + sigma * phi;
+  pi = Phi;
+  ei = delta * Phi + sigma * phi;
 }
 
 // ---- FP32 posteriors: (score, index) packed into one 64-bit key ----------
@@ -318,6 +325,8 @@ __device__ __forceinline__ void acquire_body(const AcqDev& v, const PassArgs& a,
     lam = var_s > 0.0 ? (mean_var / (a.mu_s_raw / a.fplus_raw)) / var_s : 0.0;
   const T lamT = (T)lam, fpT = (T)a.fplus_t;
 
+  bool need_phi = false;
+  for (int q = 0; q < a.n_af && q < 3; ++q) need_phi |= a.af[q] != kLCB;
   Top<T> top[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) top_init(top[q]);
@@ -327,10 +336,13 @@ __device__ __forceinline__ void acquire_body(const AcqDev& v, const PassArgs& a,
     const T m = mu[i];
     const T vv = var[i];
     const T sg = Math<T>::sqrt_(vv > T(0) ? vv : T(0));
+    T ei, pi, lcb;
+    scores3<T>(m, sg, fpT, lamT, need_phi, ei, pi, lcb);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       if (q < a.n_af) {
-        T sc = score<T>(a.af[q], m, sg, fpT, lamT);
+        const int af = a.af[q];
+        T sc = af == kEI ? ei : af == kPI ? pi : lcb;
         if (!(sc == sc)) sc = Lowest<T>::v() / T(2);   // NaN never wins
         top_insert(top[q], sc, (long long)i);
       }
