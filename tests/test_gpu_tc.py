@@ -73,6 +73,22 @@ def test_fp16x3_obs_counts_and_ragged(n):
     g.close()
 
 
+@pytest.mark.parametrize("n", [257, 300, 449])
+def test_fp16x3_two_issuers_ragged_wide(n):
+    """n > 256 (two MMA issuers, per-region rings and loaders) with a ragged last
+    chunk, on the paper-shaped 15-parameter space (the 16-coordinate bucket with
+    the d < 16 distance loop): every candidate against the oracle."""
+    sp = W.paper_shaped_space("gemm")
+    g, idx, y = state(sp, n, 6, "fp16x3", n_max=512)
+    mu, var = g.predict()
+    fit = O.gp_fit(sp.valid_coords()[idx], y, 1.5, 1.5, 1e-10)
+    rmu, rvar = O.gp_posterior(fit, sp.valid_coords())
+    em = assert_close(mu, rmu, rel=ENVELOPE["fp16x3"], floor=1.0, what="mu")
+    es = assert_close(np.sqrt(var), np.sqrt(rvar), rel=ENVELOPE["fp16x3"], floor=1.0, what="sigma")
+    print(f"gemm-shaped n = {n}: max scaled error mu {em:.2e} sigma {es:.2e}")
+    g.close()
+
+
 def test_fp16x3_ei_lockstep():
     from paper_2111_14991_gb300 import Space
     sp = W.config1_space()
