@@ -54,6 +54,11 @@ struct DevView {
   uint32_t* visited;         // [ceil(N/32)] bit i = configuration i evaluated
 
   double* X;                 // [n_max][d] coordinates of fitted observations
+  uint8_t* Xc;               // [n_max][d] value indices of fitted observations
+  const double* sqd;         // per parameter p, [m_p][m_p] (v_a - v_b)^2 of its normalized values
+  const int* sqd_meta;       // [2 d + 1]: offset of each parameter's table in sqd (then the
+                             // total), then m_p
+  int sqd_total;             // sum_p m_p^2
   float* xq;                 // [n_max / 8][ds + 2][8] per group of 8 observations: the FP32
                              // coordinates scaled as vtab32 (ds rows, rows >= d zero), then
                              // 1 / s_k^2 of the per-row power-of-two scale s_k of the split
@@ -86,6 +91,10 @@ struct DevView {
 __host__ __device__ inline size_t xq_index(int ds, int j, int slot) {
   return (size_t)(j >> 3) * (ds + 2) * 8 + (size_t)slot * 8 + (j & 7);
 }
+
+// Largest table of per-parameter squared value differences a space keeps (the
+// FP64 distances then sum d table entries instead of d differences and squares).
+constexpr size_t kSqdMaxBytes = 48 * 1024;
 
 // Per-device launch attributes, set once and shared by every host thread:
 // raise `kernel`'s dynamic shared-memory limit on the current device to at

@@ -65,7 +65,11 @@ __device__ __forceinline__ void slice_groups(int q_lo, int q_hi, const double* K
   }
 }
 
-template <int BM>
+// TAB: the space keeps its per-parameter tables of squared value differences
+// (small value lists): r^2 is then a sum of d table entries, addressed by the
+// candidate's and the observation's value indices, instead of d differences
+// and squares on the narrow FP64 pipe.
+template <int BM, bool TAB>
 __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int n, int n_pad) {
   constexpr int TM = BM / 16;             // rows per thread
   extern __shared__ double smem[];
@@ -73,9 +77,15 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
   const int ldk = n_pad + 1;
   double* Ks = smem;                      // [BM][ldk]
   double* Ls = Ks + BM * ldk;             // [kBK][kBN + 1]
-  double* Xs = Ls + kBK * (kBN + 1);      // [d][n_pad]
-  double* Cs = Xs + d * n_pad;            // [BM][d]
-  double* Bs = Cs + BM * d;               // [n_pad]
+  double* Bs = Ls + kBK * (kBN + 1);      // [n_pad]
+  // coordinates (!TAB): Xs [d][n_pad], Cs [BM][d]; tables (TAB): Ts [sqd_total],
+  // meta [2 d + 1] ints, then value indices Xc [d][n_pad] and Cc [BM][d] bytes
+  double* Xs = Bs + n_pad;
+  double* Cs = Xs + d * n_pad;
+  double* Ts = Bs + n_pad;
+  int* meta = reinterpret_cast<int*>(Ts + (TAB ? v.sqd_total : 0));
+  uint8_t* Xc = reinterpret_cast<uint8_t*>(meta + 2 * d + 1);
+  uint8_t* Cc = Xc + d * n_pad;
   __shared__ double red[kThreads / 32];
   __shared__ bool s_last;
 
@@ -83,13 +93,26 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
   const int64_t row0 = (int64_t)blockIdx.x * BM;
   const double c = sqrt(2.0 * v.nu) / v.lengthscale;
 
-  for (int e = tid; e < d * n_pad; e += kThreads) {
-    const int p = e / n_pad, j = e - p * n_pad;
-    Xs[e] = j < n ? v.X[(size_t)j * d + p] : 0.0;
-  }
-  for (int e = tid; e < BM * d; e += kThreads) {
-    const int i = e / d, p = e - i * d;
-    Cs[e] = v.vtab64[p * 256 + v.codes[(int64_t)p * v.N_pad + row0 + i]];
+  if constexpr (TAB) {
+    for (int e = tid; e < v.sqd_total; e += kThreads) Ts[e] = v.sqd[e];
+    for (int e = tid; e < 2 * d + 1; e += kThreads) meta[e] = v.sqd_meta[e];
+    for (int e = tid; e < d * n_pad; e += kThreads) {
+      const int p = e / n_pad, j = e - p * n_pad;
+      Xc[e] = j < n ? v.Xc[(size_t)j * d + p] : 0;
+    }
+    for (int e = tid; e < BM * d; e += kThreads) {
+      const int i = e / d, p = e - i * d;
+      Cc[e] = v.codes[(int64_t)p * v.N_pad + row0 + i];
+    }
+  } else {
+    for (int e = tid; e < d * n_pad; e += kThreads) {
+      const int p = e / n_pad, j = e - p * n_pad;
+      Xs[e] = j < n ? v.X[(size_t)j * d + p] : 0.0;
+    }
+    for (int e = tid; e < BM * d; e += kThreads) {
+      const int i = e / d, p = e - i * d;
+      Cs[e] = v.vtab64[p * 256 + v.codes[(int64_t)p * v.N_pad + row0 + i]];
+    }
   }
   for (int j = tid; j < n_pad; j += kThreads) Bs[j] = j < n ? v.beta[j] : 0.0;
   __syncthreads();
@@ -98,9 +121,14 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
   for (int e = tid; e < BM * n; e += kThreads) {
     const int i = e / n, j = e - i * n;
     double r2 = 0.0;
-    for (int p = 0; p < d; ++p) {
-      const double diff = Cs[i * d + p] - Xs[p * n_pad + j];
-      r2 = fma(diff, diff, r2);
+    if constexpr (TAB) {
+      for (int p = 0; p < d; ++p)
+        r2 += Ts[meta[p] + Cc[i * d + p] * meta[d + 1 + p] + Xc[p * n_pad + j]];
+    } else {
+      for (int p = 0; p < d; ++p) {
+        const double diff = Cs[i * d + p] - Xs[p * n_pad + j];
+        r2 = fma(diff, diff, r2);
+      }
     }
     Ks[i * ldk + j] = matern64(sqrt(r2), v.nu, c);
   }
@@ -195,21 +223,23 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
   }
 }
 
-template <int BM>
-size_t smem_bytes(int d, int n_pad) {
-  return sizeof(double) * ((size_t)BM * (n_pad + 1) + kBK * (kBN + 1) + (size_t)d * n_pad +
-                           (size_t)BM * d + n_pad);
+template <int BM, bool TAB>
+size_t smem_bytes(int d, int n_pad, int sqd_total) {
+  const size_t common = sizeof(double) * ((size_t)BM * (n_pad + 1) + kBK * (kBN + 1) + n_pad);
+  if (!TAB) return common + sizeof(double) * ((size_t)d * n_pad + (size_t)BM * d);
+  return common + sizeof(double) * (size_t)sqd_total + sizeof(int) * (2 * (size_t)d + 1) +
+         (size_t)d * n_pad + (size_t)BM * d;
 }
 
-template <int BM>
+template <int BM, bool TAB>
 int launch_bm(const DevView& v, int n, cudaStream_t s) {
   const int n_pad = ((n + kBK - 1) / kBK) * kBK;
-  const size_t sm = smem_bytes<BM>(v.d, n_pad);
+  const size_t sm = smem_bytes<BM, TAB>(v.d, n_pad, v.sqd_total);
   static size_t configured[kMaxDevices] = {};
-  if (!ensure_dynamic_smem((const void*)predict_f64_kernel<BM>, configured, sm)) return -1;
+  if (!ensure_dynamic_smem((const void*)predict_f64_kernel<BM, TAB>, configured, sm)) return -1;
   const int grid = (int)(v.N_pad / BM);
   if (grid > v.max_partials) return -1;
-  predict_f64_kernel<BM><<<grid, kThreads, sm, s>>>(v, n, n_pad);
+  predict_f64_kernel<BM, TAB><<<grid, kThreads, sm, s>>>(v, n, n_pad);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -217,7 +247,8 @@ int launch_bm(const DevView& v, int n, cudaStream_t s) {
 
 int launch_predict_f64(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStream_t s) {
   if (n < 1) return -1;
-  return n <= 256 ? launch_bm<64>(v, n, s) : launch_bm<32>(v, n, s);
+  if (v.sqd) return n <= 256 ? launch_bm<64, true>(v, n, s) : launch_bm<32, true>(v, n, s);
+  return n <= 256 ? launch_bm<64, false>(v, n, s) : launch_bm<32, false>(v, n, s);
 }
 
 }  // namespace bo

@@ -77,7 +77,8 @@ size_t space_device_bytes(int d, int64_t N, int n_max, int precision, int num_sm
   const size_t n = (size_t)((n_max + 31) / 32 * 32);
   const size_t fsz = precision == BO_PREC_FP64 ? 8 : 4;
   size_t t = r(d * N_pad) + r(d * 256 * 8) + r(d * 256 * 4) + r((N_pad / 32 + 1) * 4);
-  t += r(n * d * 8) + r(n * 8) + r(n * n * 8) + r(n * 8);
+  t += r(n * d * 8) + r(n * d) + r(kSqdMaxBytes) + r((2 * BO_MAX_PARAMS + 1) * 4);
+  t += r(n * 8) + r(n * n * 8) + r(n * 8);
   if (precision != BO_PREC_FP64) {
     t += r((size_t)(tc_dim_bucket(d) + 2) * n * 4);
     t += (precision == BO_PREC_TF32 ? 1 : 2) * r(lsplit_bytes((int)n, precision));
@@ -483,6 +484,22 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   TRY(dalloc_n(s, (size_t)D.d * 256, &vt32));
   TRY(dalloc_n(s, (size_t)N_pad / 32 + 1, &v.visited));
   TRY(dalloc_n(s, (size_t)n_alloc * D.d, &v.X));
+  TRY(dalloc_n(s, (size_t)n_alloc * D.d, &v.Xc));
+  // per-parameter tables of squared value differences, when they are small
+  std::vector<int> sqd_meta(2 * D.d + 1, 0);
+  size_t sqd_total = 0;
+  for (int p = 0; p < D.d; ++p) {
+    sqd_meta[p] = (int)sqd_total;
+    sqd_meta[D.d + 1 + p] = D.n_values[p];
+    sqd_total += (size_t)D.n_values[p] * D.n_values[p];
+  }
+  sqd_meta[D.d] = (int)sqd_total;
+  double* dsqd = nullptr;
+  int* dmeta = nullptr;
+  if (sqd_total * sizeof(double) <= kSqdMaxBytes) {
+    TRY(dalloc_n(s, sqd_total, &dsqd));
+    TRY(dalloc_n(s, sqd_meta.size(), &dmeta));
+  }
   v.ds = D.precision == BO_PREC_FP64 ? 0 : tc_dim_bucket(D.d);
   if (D.precision != BO_PREC_FP64) TRY(dalloc_n(s, (size_t)(v.ds + 2) * n_alloc, &v.xq));
   TRY(dalloc_n(s, (size_t)n_alloc, &v.y));
@@ -504,6 +521,9 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
 #undef TRY
   v.codes = dcodes;
   v.vtab64 = vt64;
+  v.sqd = dsqd;
+  v.sqd_meta = dmeta;
+  v.sqd_total = dsqd ? (int)sqd_total : 0;
   v.vtab32 = vt32;
   v.mu = mu;
   v.var = var;
@@ -515,7 +535,21 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
       t64[(size_t)p * 256 + i] = D.values[p][i];
       t32[(size_t)p * 256 + i] = (float)(D.values[p][i] * cs);
     }
+  // (v_a - v_b)^2 rounded once, as the distance loops would form each term
+  std::vector<double> sqd(dsqd ? sqd_total : 0);
+  for (int p = 0; dsqd && p < D.d; ++p) {
+    const int m = D.n_values[p];
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b) {
+        const double diff = D.values[p][a] - D.values[p][b];
+        sqd[(size_t)sqd_meta[p] + (size_t)a * m + b] = diff * diff;
+      }
+  }
   cudaError_t e = cudaMemcpyAsync(dcodes, codes.data(), codes.size(), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && dsqd)
+    e = cudaMemcpyAsync(dsqd, sqd.data(), sqd.size() * 8, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && dmeta)
+    e = cudaMemcpyAsync(dmeta, sqd_meta.data(), sqd_meta.size() * 4, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(vt64, t64.data(), t64.size() * 8, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(vt32, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMallocHost(&s->host_result, sizeof(bo_pass_result));

@@ -65,6 +65,7 @@ __device__ __forceinline__ void obs_k_body(const DevView& v, int n, long long id
   if (block == 0 && threadIdx.x < v.d) {
     const double x = coord64(v, idx, threadIdx.x);
     v.X[(size_t)n * v.d + threadIdx.x] = x;
+    v.Xc[(size_t)n * v.d + threadIdx.x] = v.codes[(int64_t)threadIdx.x * v.N_pad + idx];
     if (v.xq) v.xq[xq_index(v.ds, n, threadIdx.x)] = (float)(x * (1.4426950408889634 * c));
   }
   if (block == 0 && threadIdx.x == 0) {
@@ -73,9 +74,17 @@ __device__ __forceinline__ void obs_k_body(const DevView& v, int n, long long id
   }
   if (j < n) {
     double r2 = 0.0;
-    for (int p = 0; p < v.d; ++p) {
-      const double diff = coord64(v, idx, p) - v.X[(size_t)j * v.d + p];
-      r2 = fma(diff, diff, r2);
+    if (v.sqd) {   // the prediction pass's arithmetic: a sum of tabulated squared differences
+      for (int p = 0; p < v.d; ++p) {
+        const int m = v.sqd_meta[v.d + 1 + p];
+        const int a = v.codes[(int64_t)p * v.N_pad + idx], b = v.Xc[(size_t)j * v.d + p];
+        r2 += v.sqd[v.sqd_meta[p] + a * m + b];
+      }
+    } else {
+      for (int p = 0; p < v.d; ++p) {
+        const double diff = coord64(v, idx, p) - v.X[(size_t)j * v.d + p];
+        r2 = fma(diff, diff, r2);
+      }
     }
     v.kvec[j] = matern64(sqrt(r2), v.nu, c);
   }
