@@ -46,7 +46,7 @@ FP64_PEAK_TFLOPS = 1.25
 # dram bytes per launch of the dominant kernel from an ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (null once the source changes)
 TRAFFIC = {
-    "predict_f64": [{"bytes_per_launch": 1419776 + 0, "src_sha": "67487f6f85df9915", "n": 220, "N": 113247,
+    "predict_f64": [{"bytes_per_launch": 1117440 + 0, "src_sha": "7db7286ecbec0617", "n": 220, "N": 113247,
                      "capture": "profiles/predict_f64_gemm7p_n220.md"}],
     "predict_tc_fp16x3": [
         {"bytes_per_launch": 10716672 + 3584, "src_sha": "881cb10161712188", "n": 512, "N": 1032469,
