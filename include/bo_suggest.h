@@ -67,7 +67,8 @@ enum {
   BO_PREC_FP64 = 0,    /* FP64 on CUDA cores                                       */
   BO_PREC_FP16X3 = 1,  /* tcgen05 f16 hi/lo split, 3 products, FP32 accumulate     */
   BO_PREC_BF16X3 = 2,  /* tcgen05 bf16 hi/lo split, 3 products, FP32 accumulate    */
-  BO_PREC_TF32 = 3     /* tcgen05 tf32, 1 product, FP32 accumulate                 */
+  BO_PREC_TF32 = 3,    /* tcgen05 tf32, 1 product, FP32 accumulate                 */
+  BO_PREC_TF32X3 = 4   /* tcgen05 tf32 hi/lo split, 3 products, FP32 accumulate    */
 };
 
 /* initial sample (Sec. III-E; Table I selects maximin):
@@ -265,8 +266,9 @@ int bo_batch_launch_count(const bo_batch* batch, int64_t* out);
 /* Time candidate pipeline shapes of the prediction launch (depth of the K*
  * ring, slots of the L^-1 ring, resident L^-1 pieces or not) on the space's
  * or batch's current state, `reps` launches each with CUDA events, and keep
- * the fastest for every later launch of the same precision, dimension bucket
- * and padded observation count (per process).  The launches recompute the
+ * the fastest for every later launch of the same precision, Matern nu (3/2
+ * or 5/2, Sec. III-B: separate kernel instantiations), dimension bucket and
+ * padded observation count (per process).  The launches recompute the
  * current posterior (same values).  bo_batch_autotune times the batch's last
  * bo_batch_suggest pass (BO_ERR_STATE before one).  Reduced precision only. */
 typedef struct bo_tune_result {
@@ -279,6 +281,12 @@ typedef struct bo_tune_result {
 } bo_tune_result;
 int bo_autotune(bo_space* space, int32_t reps, bo_tune_result* out);
 int bo_batch_autotune(bo_batch* batch, int32_t reps, bo_tune_result* out);
+/* The shape stored for the key of the space's next prediction launch (its
+ * precision, nu, dimension bucket and padded observation count) in
+ * stages_a / b_slots / b_resident (tried, best_ms, default_ms zero), or
+ * BO_ERR_STATE when the autotuner has stored none for that key (or before the
+ * first valid observation).  Host only, no device work. */
+int bo_tuned_shape(const bo_space* space, bo_tune_result* out);
 
 /* ---- serving: continuous batching of many sessions ----------------------- */
 /* A request loop for many concurrent tuning sessions.  A worker thread takes,
@@ -355,9 +363,12 @@ int bo_server_destroy(bo_server* server);
  *             mean variance, top-3 per acquisition function)
  * stream      cudaStream_t (NULL = legacy default stream)
  *
- * Returns BO_ERR_CAPACITY for n_cand > BO_NOALLOC_MAX_CAND (the scratch holds
- * the partial results of at most 1,024 blocks of 4,096 candidates),
- * BO_ERR_ARG for bad arguments, BO_ERR_CUDA if a launch fails.
+ * Returns BO_ERR_CAPACITY for n_cand > BO_NOALLOC_MAX_CAND, BO_ERR_ARG for
+ * bad arguments (including an explore mode other than CV or CONST),
+ * BO_ERR_NOT_POSITIVE when CV lacks positive f+ and mu_s, BO_ERR_CUDA if a
+ * launch fails.  The scratch holds the partial top-k lists of the at most
+ * 1,024 blocks one call launches; the blocks stride over the candidates, and
+ * the cap bounds the work of one call (16 candidates per thread at the cap).
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress, no allocation) with that device current; make that
  * first call before any stream capture.  Every call shares the one array and

@@ -21,7 +21,7 @@ ERRORS = {1: "BO_ERR_ARG", 2: "BO_ERR_INDEX", 3: "BO_ERR_DUPLICATE", 4: "BO_ERR_
           9: "BO_ERR_NOT_POSITIVE", 10: "BO_ERR_STATE", 11: "BO_ERR_CAPACITY"}
 AF = {"ei": 0, "poi": 1, "pi": 1, "lcb": 2, "multi": 3, "advanced_multi": 4}
 AF_NAMES = {0: "ei", 1: "poi", 2: "lcb", -1: None}
-PRECISION = {"fp64": 0, "fp16x3": 1, "bf16x3": 2, "tf32": 3}
+PRECISION = {"fp64": 0, "fp16x3": 1, "bf16x3": 2, "tf32": 3, "tf32x3": 4}
 INIT = {"random": 0, "lhs": 1, "maximin": 2}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -116,6 +116,7 @@ SIGNATURES = {
                                         C.POINTER(SuggestInfo)]),
     "bo_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(TuneResult)]),
     "bo_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(TuneResult)]),
+    "bo_tuned_shape": (C.c_int, [C.c_void_p, C.POINTER(TuneResult)]),
     "bo_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
     "bo_server_open": (C.c_int, [C.c_void_p, C.POINTER(SpaceDesc), C.POINTER(C.c_int64)]),
     "bo_server_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_int32, C.c_uint64]),
@@ -299,6 +300,15 @@ class Space:
     def autotune(self, reps=3):
         r = TuneResult()
         _check(lib().bo_autotune(self._h, int(reps), C.byref(r)))
+        return _tune_dict(r)
+
+    def tuned_shape(self):
+        """The autotuner's stored shape for this space's next launch key, or None."""
+        r = TuneResult()
+        rc = lib().bo_tuned_shape(self._h, C.byref(r))
+        if rc == 10:                     # BO_ERR_STATE: nothing stored for the key
+            return None
+        _check(rc)
         return _tune_dict(r)
 
     def predict_enqueue(self):

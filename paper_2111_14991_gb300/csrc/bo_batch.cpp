@@ -415,7 +415,7 @@ int bo_batch_autotune(bo_batch* b, int32_t reps, bo_tune_result* out) {
   cudaSetDevice(b->device);
   BO_CUDA(cudaStreamSynchronize(b->bs));
   const TcBatchLaunch L = b->last;
-  const int rc = autotune_shapes(b->bs, reps, b->precision, L.dmax, L.n_pad_max, true,
+  const int rc = autotune_shapes(b->bs, reps, b->precision, L.nu, L.dmax, L.n_pad_max, true,
                                  [&] { return launch_predict_tc_batch(L, b->bs); }, out);
   b->gkey.clear();               // captured graphs hold the old shape
   b->seen_key.clear();

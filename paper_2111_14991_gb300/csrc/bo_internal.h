@@ -68,8 +68,8 @@ struct DevView {
   double* y;                 // [n_max] raw fitted values
   double* linv;              // [n_max][n_max] L^-1, row-major, lower triangular
   double* beta;              // [n_max] L^-1 y~
-  uint8_t* lsplit_hi;        // reduced-precision chunked copy of L^-1 (hi or tf32)
-  uint8_t* lsplit_lo;        // (lo part; unused for tf32)
+  uint8_t* lsplit_hi;        // reduced-precision chunked copy of L^-1 (hi part, or the single tf32)
+  uint8_t* lsplit_lo;        // (lo part; unused for the single tf32 form)
 
   void* mu;                  // [N_pad] posterior mean (double for FP64, else float)
   void* var;                 // [N_pad] posterior variance
@@ -230,7 +230,9 @@ int launch_predict_tc_batch(const TcBatchLaunch& L, cudaStream_t s);
 // Autotuner hooks: launches on this thread use `shape` while it is forced
 // (nullptr ends it); a stored shape applies to every later launch of its key.
 void tc_force_shape(const TcShape* shape);
-void tc_store_shape(int precision, int dmax, int n_pad, bool batched, const TcShape& shape);
+void tc_store_shape(int precision, double nu, int dmax, int n_pad, bool batched, const TcShape& shape);
+// The stored shape of a key, if the autotuner has chosen one.
+bool tc_stored_shape(int precision, double nu, int dmax, int n_pad, bool batched, TcShape* shape);
 int launch_acquire(const DevView& v, const PassArgs& a, cudaStream_t s);
 int launch_acquire(const AcqDev& v, const PassArgs& a, bool f64, cudaStream_t s);
 // Blocks of an acquisition pass over n_cand candidates, per_thread candidates
@@ -245,6 +247,14 @@ int launch_acquire_batch(const AcqItem* items, const int* block_item, const int*
 inline double coord_scale(double nu, double lengthscale) {
   return 1.4426950408889634 * __builtin_sqrt(2.0 * nu) / lengthscale;
 }
+
+// Element width in bytes of the reduced-precision L^-1 copy and of the K*
+// operand (4 for the TF32 forms, 2 for the 16-bit forms), and the number of
+// parts of each (hi and lo, or a single TF32 part).
+__host__ __device__ constexpr int split_elem_bytes(int precision) {
+  return precision == BO_PREC_TF32 || precision == BO_PREC_TF32X3 ? 4 : 2;
+}
+__host__ __device__ constexpr int split_parts(int precision) { return precision == BO_PREC_TF32 ? 1 : 2; }
 
 // Record an error for bo_last_error() on this thread; returns code.
 int report_error(int code, const char* msg);

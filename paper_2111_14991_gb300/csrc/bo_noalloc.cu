@@ -14,8 +14,12 @@
 namespace bo {
 namespace {
 
-constexpr int kNoallocBlocks = 1024;           // partial lists the array holds
-constexpr int64_t kCandPerBlock = 256 * 16;    // candidates one acquisition block covers
+// The array holds the partial top-k lists of kNoallocBlocks blocks, the most
+// one call launches; the blocks stride over the candidates, so the array does
+// not bound n_cand.  BO_NOALLOC_MAX_CAND bounds the work of one call instead:
+// at the cap each thread of the 1,024 blocks of 256 threads scores 16 candidates.
+constexpr int kNoallocBlocks = 1024;
+constexpr int64_t kMaxCandPerThread = 16;
 
 struct NoallocScratch {
   unsigned int counter;                        // last-block counter, zero before a launch
@@ -26,7 +30,7 @@ struct NoallocScratch {
   TopEntry partial[kNoallocBlocks * 9];        // [block][af][rank]
 };
 static_assert(sizeof(NoallocScratch) == 147520, "documented scratch size");
-static_assert((int64_t)kNoallocBlocks * kCandPerBlock == BO_NOALLOC_MAX_CAND, "documented limit");
+static_assert((int64_t)kNoallocBlocks * 256 * kMaxCandPerThread == BO_NOALLOC_MAX_CAND, "documented limit");
 
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
 
@@ -78,6 +82,8 @@ extern "C" int bo_acquire_noalloc(const void* mu, const void* var, const uint32_
     return report_error(BO_ERR_ARG, "bad n_af or n_unvisited");
   for (int q = 0; q < p->n_af; ++q)
     if (p->af[q] < BO_AF_EI || p->af[q] > BO_AF_LCB) return report_error(BO_ERR_ARG, "bad af id");
+  if (p->explore != BO_EXPLORE_CV && p->explore != BO_EXPLORE_CONST)
+    return report_error(BO_ERR_ARG, "explore must be BO_EXPLORE_CV or BO_EXPLORE_CONST");
   if (p->explore == BO_EXPLORE_CV && !(p->fplus_raw > 0.0 && p->mu_s_raw > 0.0))
     return report_error(BO_ERR_NOT_POSITIVE, "contextual variance needs f+ > 0 and mu_s > 0");
   int err = BO_OK;
@@ -110,8 +116,6 @@ extern "C" int bo_acquire_noalloc(const void* mu, const void* var, const uint32_
   ad.counter = &s->counter;
   ad.max_blocks = kNoallocBlocks;
   ad.result = result;
-  if (acquire_grid(p->n_cand, kNoallocBlocks) * kCandPerBlock < p->n_cand)
-    return report_error(BO_ERR_CAPACITY, "grid does not cover the candidates");
   if (launch_acquire(ad, a, f64 != 0, st) < 0) return report_error(BO_ERR_CUDA, "acquisition launch failed");
   return BO_OK;
 }

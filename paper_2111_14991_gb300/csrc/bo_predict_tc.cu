@@ -7,8 +7,10 @@
 // mu does not depend on the split contraction; the contraction V = K* L^-T,
 // needed for the variance, runs on the tensor cores with FP32 accumulation in
 // tensor memory, with the operands split to recover precision:
-//   FP16X3 / BF16X3: K* = Kh + Kl and L^-1 = Lh + Ll (per-row power-of-two
-//     scaled), V ~ Kh Lh + Kh Ll + Kl Lh  (three MMAs per k-step)
+//   FP16X3 / BF16X3 / TF32X3: K* = Kh + Kl and L^-1 = Lh + Ll (per-row
+//     power-of-two scaled), V ~ Kh Lh + Kh Ll + Kl Lh  (three MMAs per
+//     k-step); a 16-bit or TF32 part has 11 (FP16, TF32) or 8 (BF16)
+//     significant bits, so FP16X3 and TF32X3 carry about 22 bits
 //   TF32: one MMA on TF32-rounded operands.
 // The FP64 L^-1, beta and the update stay in FP64 (bo_update.cu), which
 // writes the split copy of each new row once.
@@ -252,7 +254,7 @@ __host__ __device__ __forceinline__ uint32_t instr_desc(int fmt, int m, int n) {
 
 template <int MODE>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if constexpr (MODE == BO_PREC_TF32) {
+  if constexpr (split_elem_bytes(MODE) == 4) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
@@ -394,6 +396,7 @@ __device__ __forceinline__ uint64_t matern2(uint64_t u2p) {
 // than DMAX coordinates (d, warp-uniform).
 template <int MODE, int DMAX, bool CHECK>
 __device__ __forceinline__ void sq_dist(const uint64_t* xcp, uint32_t grp, int d, uint64_t* r2p) {
+  constexpr bool kWide = split_elem_bytes(MODE) == 2;   // 8 observations per thread and chunk, else 4
   const uint64_t eps = dup2(1e-30f);
   r2p[0] = r2p[1] = r2p[2] = r2p[3] = eps;
 #pragma unroll
@@ -405,7 +408,7 @@ __device__ __forceinline__ void sq_dist(const uint64_t* xcp, uint32_t grp, int d
     r2p[0] = fma2(df, df, r2p[0]);
     df = sub2(xcp[p], o1);
     r2p[1] = fma2(df, df, r2p[1]);
-    if constexpr (MODE != BO_PREC_TF32) {
+    if constexpr (kWide) {
       lds2x64(grp + (uint32_t)(p * 32 + 16), o0, o1);
       df = sub2(xcp[p], o0);
       r2p[2] = fma2(df, df, r2p[2]);
@@ -455,7 +458,7 @@ template <int MODE, int DMAX, bool NU52>
 __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_constant__ TcParams P) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int CW = MODE == BO_PREC_TF32 ? 16 : 32;   // observations per K chunk
+  constexpr int CW = kChunkBytes / split_elem_bytes(MODE);   // observations per K chunk: 32 or 16
   const int cw = CW, parts = P.parts, SA = P.stages_a, XB = P.xs_bufs;
   uint8_t* sa = smem;                                   // [SA][parts][8 KB]
   uint8_t* sb = smem + P.off_b;                         // B slots or resident pieces
@@ -597,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
             uint64_t a0, a1;
             lds2x64(arow, a0, a1);
             m2 = fma2(kv[1], a1, fma2(kv[0], a0, m2));
-            if constexpr (MODE != BO_PREC_TF32) {
+            if constexpr (CW == 32) {
               lds2x64(arow + 16, a0, a1);
               m2 = fma2(kv[3], a1, fma2(kv[2], a0, m2));
             }
@@ -616,6 +619,17 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
             upk2(kv[0], k0, k1);
             upk2(kv[1], k2, k3);
             st_shared_v4(stage, to_tf32(k0), to_tf32(k1), to_tf32(k2), to_tf32(k3));
+          } else if constexpr (MODE == BO_PREC_TF32X3) {
+            // hi = TF32 rounding of k, lo = TF32 rounding of the (exact) residual k - hi
+            float k0, k1, k2, k3;
+            upk2(kv[0], k0, k1);
+            upk2(kv[1], k2, k3);
+            const uint32_t h0 = to_tf32(k0), h1 = to_tf32(k1), h2 = to_tf32(k2), h3 = to_tf32(k3);
+            float r0, r1, r2, r3;
+            upk2(sub2(kv[0], pk2(__uint_as_float(h0), __uint_as_float(h1))), r0, r1);
+            upk2(sub2(kv[1], pk2(__uint_as_float(h2), __uint_as_float(h3))), r2, r3);
+            st_shared_v4(stage, h0, h1, h2, h3);
+            st_shared_v4(stage + kPartBytes, to_tf32(r0), to_tf32(r1), to_tf32(r2), to_tf32(r3));
           } else {
             uint32_t h[4], l[4];
 #pragma unroll
@@ -904,8 +918,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     const int l_me = warp == kLoadWarp ? 0 : 1;
     const bool split = P.issuers == 2 && !P.b_resident;
     if (lane == 0 && (l_me == 0 || split)) {
-      const int eb = MODE == BO_PREC_TF32 ? 4 : 2;
-      const int ccw = kChunkBytes / eb;
+      const int ccw = kChunkBytes / split_elem_bytes(MODE);
       const uint32_t b_base = smem_addr(sb);
       bool ok = true, b_loaded = false;
       int issued[kMaxBSlots], last_phase[kMaxBSlots], xs_issued[2] = {0, 0}, xs_phase[2] = {0, 0};
@@ -1008,15 +1021,16 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
 // dimension buckets: the distance loop runs over DMAX zero-padded coordinates
 int dim_bucket(int d) { return d <= 4 ? 4 : d <= 7 ? 7 : d <= 9 ? 9 : 16; }
 
-// Pipeline shapes chosen by the autotuner, per (precision, dim bucket, padded n, batched).
+// Pipeline shapes chosen by the autotuner, per (precision, Matern nu = 5/2,
+// dim bucket, padded n, batched): each key is its own kernel instantiation.
 std::mutex g_tune_mu;
-std::map<std::array<int, 4>, TcShape> g_tuned;
+std::map<std::array<int, 5>, TcShape> g_tuned;
 thread_local const TcShape* g_forced = nullptr;   // a shape being timed by the autotuner
 
-TcShape shape_for(int precision, int dmax, int n_pad, bool batched) {
+TcShape shape_for(int precision, double nu, int dmax, int n_pad, bool batched) {
   if (g_forced) return *g_forced;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  auto it = g_tuned.find({precision, dmax, n_pad, batched ? 1 : 0});
+  auto it = g_tuned.find({precision, nu == 2.5 ? 1 : 0, dmax, n_pad, batched ? 1 : 0});
   return it == g_tuned.end() ? TcShape{} : it->second;
 }
 
@@ -1047,9 +1061,14 @@ int dispatch(const TcParams& P, int precision, double nu, int dmax, size_t smem,
     case BO_PREC_BF16X3:
       return nu52 ? launch_dims<BO_PREC_BF16X3, true>(P, dmax, smem, grid, s)
                   : launch_dims<BO_PREC_BF16X3, false>(P, dmax, smem, grid, s);
-    default:
+    case BO_PREC_TF32X3:
+      return nu52 ? launch_dims<BO_PREC_TF32X3, true>(P, dmax, smem, grid, s)
+                  : launch_dims<BO_PREC_TF32X3, false>(P, dmax, smem, grid, s);
+    case BO_PREC_TF32:
       return nu52 ? launch_dims<BO_PREC_TF32, true>(P, dmax, smem, grid, s)
                   : launch_dims<BO_PREC_TF32, false>(P, dmax, smem, grid, s);
+    default:
+      return -1;
   }
 }
 
@@ -1058,9 +1077,8 @@ int dispatch(const TcParams& P, int precision, double nu, int dmax, size_t smem,
 // the B pieces of the (single) space may stay resident.  Returns the dynamic
 // shared-memory size, 0 if nothing fits.
 size_t plan_smem(TcParams& P, int precision, int n_pad_max, int dmax, bool resident_ok, const TcShape& shape) {
-  const int eb = precision == BO_PREC_TF32 ? 4 : 2;
-  P.cw = kChunkBytes / eb;
-  P.parts = precision == BO_PREC_TF32 ? 1 : 2;
+  P.cw = kChunkBytes / split_elem_bytes(precision);
+  P.parts = split_parts(precision);
   int cols = 32;
   while (cols < n_pad_max) cols <<= 1;
   if (cols > 512) return 0;
@@ -1146,7 +1164,7 @@ TcSess tc_session(const DevView& v, int n) {
   S.n = n;
   S.n_pad = (n + 31) / 32 * 32;
   S.n_max = v.n_max;
-  S.chunks = S.n_pad / (kChunkBytes / (v.precision == BO_PREC_TF32 ? 4 : 2));
+  S.chunks = S.n_pad / (kChunkBytes / split_elem_bytes(v.precision));
   S.num_tiles = (int)(v.N_pad / kRows);
   return S;
 }
@@ -1163,7 +1181,7 @@ int launch_predict_tc(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStre
   P.status = &v.stats->status;
   const int dmax = dim_bucket(v.d);
   const size_t smem = plan_smem(P, v.precision, P.s0.n_pad, dmax, true,
-                                shape_for(v.precision, dmax, P.s0.n_pad, false));
+                                shape_for(v.precision, v.nu, dmax, P.s0.n_pad, false));
   if (!smem) return -1;
   const int grid = std::min(P.s0.num_tiles, num_sms());
   if (grid > v.max_partials) return -1;
@@ -1226,7 +1244,7 @@ int launch_predict_tc_batch(const TcBatchLaunch& L, cudaStream_t s) {
   P.status = L.status;
   P.xs_bufs = 2;
   const size_t smem = plan_smem(P, L.precision, L.n_pad_max, L.dmax, false,
-                                shape_for(L.precision, L.dmax, L.n_pad_max, true));
+                                shape_for(L.precision, L.nu, L.dmax, L.n_pad_max, true));
   if (!smem) return -1;
   return dispatch(P, L.precision, L.nu, L.dmax, smem, L.grid, s);
 }
@@ -1235,9 +1253,17 @@ int tc_dim_bucket(int d) { return dim_bucket(d); }
 
 void tc_force_shape(const TcShape* shape) { g_forced = shape; }
 
-void tc_store_shape(int precision, int dmax, int n_pad, bool batched, const TcShape& shape) {
+void tc_store_shape(int precision, double nu, int dmax, int n_pad, bool batched, const TcShape& shape) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tuned[{precision, dmax, n_pad, batched ? 1 : 0}] = shape;
+  g_tuned[{precision, nu == 2.5 ? 1 : 0, dmax, n_pad, batched ? 1 : 0}] = shape;
+}
+
+bool tc_stored_shape(int precision, double nu, int dmax, int n_pad, bool batched, TcShape* shape) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find({precision, nu == 2.5 ? 1 : 0, dmax, n_pad, batched ? 1 : 0});
+  if (it == g_tuned.end()) return false;
+  *shape = it->second;
+  return true;
 }
 
 }  // namespace bo

@@ -81,7 +81,7 @@ size_t space_device_bytes(int d, int64_t N, int n_max, int precision, int num_sm
   t += r(n * 8) + r(n * n * 8) + r(n * 8);
   if (precision != BO_PREC_FP64) {
     t += r((size_t)(tc_dim_bucket(d) + 2) * n * 4);
-    t += (precision == BO_PREC_TF32 ? 1 : 2) * r(lsplit_bytes((int)n, precision));
+    t += split_parts(precision) * r(lsplit_bytes((int)n, precision));
   }
   t += 2 * r(N_pad * fsz) + r((N_pad / 32 + num_sms) * 8) + 2 * r(n * 8) + r(8 * n * 8) + r(sizeof(DevStats));
   t += r((size_t)4 * num_sms * 9 * sizeof(TopEntry)) + r(1024 * sizeof(bo_pass_result));
@@ -393,7 +393,7 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   if (!(D.lengthscale > 0) || !(D.jitter >= 0)) return fail(BO_ERR_ARG, "bad lengthscale / jitter");
   if (D.af < BO_AF_EI || D.af > BO_AF_ADV_MULTI) return fail(BO_ERR_ARG, "bad af");
   if (D.explore != BO_EXPLORE_CV && D.explore != BO_EXPLORE_CONST) return fail(BO_ERR_ARG, "bad explore");
-  if (D.precision < BO_PREC_FP64 || D.precision > BO_PREC_TF32) return fail(BO_ERR_ARG, "bad precision");
+  if (D.precision < BO_PREC_FP64 || D.precision > BO_PREC_TF32X3) return fail(BO_ERR_ARG, "bad precision");
   if (D.n_max < 1 || D.n_max > BO_MAX_OBS) return fail(BO_ERR_ARG, "n_max not in [1, %d]", BO_MAX_OBS);
   if (D.skip_threshold < 0 || D.n_init < 0 || D.init_designs < 0) return fail(BO_ERR_ARG, "negative count");
   if (D.init_mode < BO_INIT_RANDOM || D.init_mode > BO_INIT_MAXIMIN) return fail(BO_ERR_ARG, "bad init_mode");
@@ -507,7 +507,7 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   TRY(dalloc_n(s, (size_t)n_alloc, &v.beta));
   if (D.precision != BO_PREC_FP64) {
     TRY(dalloc_n(s, lsplit_bytes(n_alloc, D.precision), &v.lsplit_hi));
-    if (D.precision != BO_PREC_TF32) TRY(dalloc_n(s, lsplit_bytes(n_alloc, D.precision), &v.lsplit_lo));
+    if (split_parts(D.precision) == 2) TRY(dalloc_n(s, lsplit_bytes(n_alloc, D.precision), &v.lsplit_lo));
   }
   TRY(dalloc(s, (size_t)N_pad * fsz, &mu));
   TRY(dalloc(s, (size_t)N_pad * fsz, &var));
@@ -673,8 +673,23 @@ int bo_autotune(bo_space* s, int32_t reps, bo_tune_result* out) {
   cudaSetDevice(s->device);
   BO_CUDA(cudaStreamSynchronize(s->stream));
   const TcSess ts = tc_session(s->v, s->n_fit);
-  return autotune_shapes(s->stream, reps, s->desc.precision, tc_dim_bucket(s->d), ts.n_pad, false,
+  return autotune_shapes(s->stream, reps, s->desc.precision, s->desc.nu, tc_dim_bucket(s->d), ts.n_pad, false,
                          [&] { return launch_predict_tc(s->v, s->n_fit, s->N - s->n_visited, s->stream); }, out);
+}
+
+int bo_tuned_shape(const bo_space* s, bo_tune_result* out) {
+  if (!s || !out) return fail(BO_ERR_ARG, "null argument");
+  if (s->desc.precision == BO_PREC_FP64) return fail(BO_ERR_ARG, "the FP64 pass has no tensor-core shapes");
+  if (s->n_fit == 0) return fail(BO_ERR_STATE, "no valid observation to predict from");
+  const TcSess ts = tc_session(s->v, s->n_fit);
+  TcShape sh{};
+  std::memset(out, 0, sizeof *out);
+  if (!tc_stored_shape(s->desc.precision, s->desc.nu, tc_dim_bucket(s->d), ts.n_pad, false, &sh))
+    return fail(BO_ERR_STATE, "no shape stored for this launch key");
+  out->stages_a = sh.stages_a;
+  out->b_slots = sh.b_slots;
+  out->b_resident = sh.b_resident;
+  return BO_OK;
 }
 
 int bo_get_factor(bo_space* s, double* linv_out, double* beta_out, int32_t* n_out) {

@@ -221,7 +221,7 @@ int suggest_finish(bo_space* s, const bo_pass_result& r, int64_t* idx_out, bo_su
 // returning < 0 on failure) under each candidate TcShape; store and report the
 // fastest under `key`.
 template <typename Launch>
-int autotune_shapes(cudaStream_t stream, int reps, int precision, int dmax, int n_pad, bool batched,
+int autotune_shapes(cudaStream_t stream, int reps, int precision, double nu, int dmax, int n_pad, bool batched,
                     Launch launch, bo_tune_result* out);
 
 }  // namespace host
@@ -231,7 +231,7 @@ namespace bo {
 namespace host {
 
 template <typename Launch>
-int autotune_shapes(cudaStream_t stream, int reps, int precision, int dmax, int n_pad, bool batched,
+int autotune_shapes(cudaStream_t stream, int reps, int precision, double nu, int dmax, int n_pad, bool batched,
                     Launch launch, bo_tune_result* out) {
   reps = std::max(1, std::min(reps, 50));
   cudaEvent_t e0, e1;
@@ -279,7 +279,7 @@ int autotune_shapes(cudaStream_t stream, int reps, int precision, int dmax, int 
       }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  tc_store_shape(precision, dmax, n_pad, batched, best);
+  tc_store_shape(precision, nu, dmax, n_pad, batched, best);
   if (out) {
     out->stages_a = best.stages_a;
     out->b_slots = best.b_slots;

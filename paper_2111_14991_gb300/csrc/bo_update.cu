@@ -29,11 +29,6 @@ __device__ __forceinline__ double coord64(const DevView& v, int64_t idx, int p) 
   return v.vtab64[p * 256 + v.codes[(int64_t)p * v.N_pad + idx]];
 }
 
-// Element width and chunk width (elements of j per kChunkBytes) of the split copy.
-__host__ __device__ __forceinline__ int split_elem_bytes(int precision) {
-  return precision == BO_PREC_TF32 ? 4 : 2;
-}
-
 // Byte offset of element (row k, column j) of L^-1 in the chunked copy.
 // Chunk c holds columns [c*CW, (c+1)*CW) of rows k >= c*CW, in the K-major
 // no-swizzle core-matrix layout the tensor core reads: 8-row x 16-byte core
@@ -219,6 +214,11 @@ __device__ __forceinline__ void obs_finish_body(const DevView& v, int n) {
       uint32_t u;
       asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
       *reinterpret_cast<uint32_t*>(v.lsplit_hi + off) = u;
+      if (v.precision == BO_PREC_TF32X3) {   // lo = the rounding residual, itself rounded to TF32
+        uint32_t w;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w) : "f"(x - __uint_as_float(u)));
+        *reinterpret_cast<uint32_t*>(v.lsplit_lo + off) = w;
+      }
     }
   }
 }

@@ -74,3 +74,18 @@ def test_no_gpu_means_loud_failure():
     from paper_2111_14991_gb300 import Space
     with pytest.raises(RuntimeError):
         Space([[0.0, 1.0]])
+
+
+def test_noalloc_argument_checks_without_device(library):
+    """bo_acquire_noalloc rejects an oversized count and an unknown explore mode
+    before it touches any device (so this runs on a machine without a GPU)."""
+    from paper_2111_14991_gb300 import bo
+    p = bo.AcqParams()
+    p.n_cand, p.n_unvisited, p.n_af = 4194304 + 1, 10, 1
+    with pytest.raises(bo.BOError) as e:
+        bo.acquire_noalloc(16, 16, 16, 0, p, 16, 0)
+    assert e.value.code == 11
+    p.n_cand, p.explore = 100, 7
+    with pytest.raises(bo.BOError) as e:
+        bo.acquire_noalloc(16, 16, 16, 0, p, 16, 0)
+    assert e.value.code == 1 and "explore" in str(e.value)

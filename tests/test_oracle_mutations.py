@@ -137,3 +137,17 @@ def test_restricted_samples_not_replaced(monkeypatch):
         return orig(grids, None, count, mode, designs, seed, draw)    # mask ignored
     monkeypatch.setattr(T_samp, "initial_design", bad)
     _fails(T_samp.test_restricted_samples_are_replaced_and_valid_ones_kept, "lhs")
+
+
+def test_column_major_enumeration(monkeypatch):
+    import test_oracle_space as T_sp
+
+    def bad(sizes, invalid_mask=None):          # first parameter fastest
+        total = int(np.prod(sizes, dtype=np.int64))
+        flat = np.arange(total, dtype=np.int64)
+        if invalid_mask is not None:
+            flat = flat[np.asarray(invalid_mask).reshape(-1) == 0]
+        codes = np.stack(np.unravel_index(flat, tuple(int(s) for s in sizes), order="F"), axis=1)
+        return flat, codes
+    monkeypatch.setattr(T_sp.O, "valid_list", bad)
+    _fails(T_sp.test_valid_list_hand_enumerated)

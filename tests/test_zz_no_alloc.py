@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 from paper_2111_14991_gb300 import workloads as W
-from tolerances import REDUCED
+from tolerances import FP64, REDUCED
 
 pytestmark = pytest.mark.gpu
 
@@ -40,15 +40,20 @@ def sequential_stats(y):
     return m, (s if s != 0.0 else 1.0), min(y)
 
 
-def test_noalloc_matches_session_pass_twice():
+@pytest.mark.parametrize("precision", ["fp16x3", "fp64"])
+def test_noalloc_matches_session_pass_twice(precision):
+    """FP32 posteriors (packed score/index keys in the scratch) and FP64
+    posteriors (separate scores and indices): both partial layouts."""
     import torch
     from paper_2111_14991_gb300 import Space
     from paper_2111_14991_gb300 import bo
+    f64 = precision == "fp64"
+    tol = FP64 if f64 else REDUCED
     sp = W.config2_space()
     land = W.Landscape(sp, 3)
     idx = W.clustered_observations(land, 60, 3)
     y = [float(land.clean([i])[0]) for i in idx]
-    s = Space(sp.grids, sp.invalid, precision="fp16x3", n_max=64)
+    s = Space(sp.grids, sp.invalid, precision=precision, n_max=64)
     for i, v in zip(idx[:59], y[:59]):
         s.observe(int(i), v)
     s.replay_enqueue(idx[59:], y[59:])
@@ -61,8 +66,9 @@ def test_noalloc_matches_session_pass_twice():
     for i in idx:
         words[i >> 5] |= np.uint32(1) << np.uint32(i & 31)
     dev = torch.device("cuda")
-    t_mu = torch.tensor(mu, dtype=torch.float32, device=dev)
-    t_var = torch.tensor(var, dtype=torch.float32, device=dev)
+    ftype = torch.float64 if f64 else torch.float32
+    t_mu = torch.tensor(mu, dtype=ftype, device=dev)
+    t_var = torch.tensor(var, dtype=ftype, device=dev)
     t_vis = torch.tensor(words.view(np.int32), device=dev)
     t_res = torch.zeros(C.sizeof(bo.PassResult), dtype=torch.uint8, device=dev)
     mean, sd, ymin = sequential_stats(y)
@@ -76,7 +82,7 @@ def test_noalloc_matches_session_pass_twice():
     stream = torch.cuda.current_stream()
     for call in range(2):
         t_res.zero_()
-        bo.acquire_noalloc(t_mu.data_ptr(), t_var.data_ptr(), t_vis.data_ptr(), 0, p,
+        bo.acquire_noalloc(t_mu.data_ptr(), t_var.data_ptr(), t_vis.data_ptr(), int(f64), p,
                            t_res.data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()
         got = bo.pass_result_dict(bo.PassResult.from_buffer_copy(t_res.cpu().numpy().tobytes()))
@@ -86,7 +92,7 @@ def test_noalloc_matches_session_pass_twice():
         for q in range(3):
             for k in range(3):
                 a, b = got["top_score"][q][k], ref["top_score"][q][k]
-                assert abs(a - b) <= REDUCED["rel"] * max(abs(b), REDUCED["floor"]), (call, q, k)
+                assert abs(a - b) <= tol["rel"] * max(abs(b), tol["floor"]), (call, q, k)
             assert got["top_idx"][q][0] == ref["top_idx"][q][0] or \
                 abs(got["top_score"][q][0] - ref["top_score"][q][0]) <= 1e-6, (call, q)
 
@@ -100,3 +106,13 @@ def test_noalloc_rejects_too_many_candidates():
     with pytest.raises(bo.BOError) as e:
         bo.acquire_noalloc(16, 16, 16, 0, p, 16, 0)    # rejected before any device access
     assert e.value.code == 11 and "fixed scratch" in str(e.value)
+
+
+def test_noalloc_rejects_unknown_explore_mode():
+    from paper_2111_14991_gb300 import bo
+    p = bo.AcqParams()
+    p.n_cand, p.n_unvisited, p.n_af = 100, 10, 1
+    p.explore = 7
+    with pytest.raises(bo.BOError) as e:
+        bo.acquire_noalloc(16, 16, 16, 0, p, 16, 0)    # rejected before any device access
+    assert e.value.code == 1 and "explore" in str(e.value)
