@@ -407,6 +407,28 @@ int bo_acquire_noalloc(const void* mu, const void* var, const uint32_t* visited,
  * launch or copy fails. */
 int bo_selftest_waits(int32_t* mbar_status, int32_t* grid_status);
 
+/* ---- arithmetic peaks of the current device (measurement) ----------------- */
+/* Issue-rate probes of the units the prediction passes run on, for their
+ * roofline denominators (no counterpart in the paper): register-resident
+ * loops of 8 independent chains per thread, 64 warps per SM on every SM, best
+ * of 5 launches timed with CUDA events on the legacy default stream.
+ *   fp64_fma_tflops    DFMA (the FP64 pass), 2 flops each
+ *   fp32_fma_tflops    scalar FFMA, 2 flops each
+ *   fp32x2_fma_tflops  packed fma.rn.f32x2 (the K* producers), 4 flops each
+ *   mufu_gops          ex2.approx + rsqrt.approx (the Matern evaluation), 1 op each
+ * Synchronous, about 0.2 s; allocates and frees 256 bytes of device memory;
+ * changes no clock or other device setting.  Returns BO_ERR_ARG for a null
+ * output, BO_ERR_CUDA without a device or if a launch fails. */
+typedef struct bo_alu_peaks {
+  double fp64_fma_tflops;
+  double fp32_fma_tflops;
+  double fp32x2_fma_tflops;
+  double mufu_gops;
+  int32_t sms;
+  int32_t pad;
+} bo_alu_peaks;
+int bo_measure_alu_peaks(bo_alu_peaks* out);
+
 /* Number of kernel launches this library has issued on the space so far. */
 int bo_launch_count(const bo_space* space, int64_t* out);
 

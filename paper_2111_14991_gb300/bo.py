@@ -94,6 +94,12 @@ class ServerStats(C.Structure):
                 ("bytes_in_use", C.c_int64)]
 
 
+class AluPeaks(C.Structure):
+    _fields_ = [("fp64_fma_tflops", C.c_double), ("fp32_fma_tflops", C.c_double),
+                ("fp32x2_fma_tflops", C.c_double), ("mufu_gops", C.c_double), ("sms", C.c_int32),
+                ("pad", C.c_int32)]
+
+
 # every symbol include/bo_suggest.h declares, with (restype, argtypes)
 SIGNATURES = {
     "bo_space_desc_init": (None, [C.POINTER(SpaceDesc)]),
@@ -117,6 +123,7 @@ SIGNATURES = {
     "bo_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(TuneResult)]),
     "bo_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(TuneResult)]),
     "bo_tuned_shape": (C.c_int, [C.c_void_p, C.POINTER(TuneResult)]),
+    "bo_measure_alu_peaks": (C.c_int, [C.POINTER(AluPeaks)]),
     "bo_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
     "bo_server_open": (C.c_int, [C.c_void_p, C.POINTER(SpaceDesc), C.POINTER(C.c_int64)]),
     "bo_server_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_int32, C.c_uint64]),
@@ -484,3 +491,11 @@ def pass_result_dict(r):
                 top_score=[[r.top_score[q][k] for k in range(3)] for q in range(3)],
                 top_mu=[[r.top_mu[q][k] for k in range(3)] for q in range(3)],
                 top_sigma=[[r.top_sigma[q][k] for k in range(3)] for q in range(3)])
+
+
+def measure_alu_peaks():
+    """bo_measure_alu_peaks on the current device: FP64 / FP32 / f32x2 FMA rates
+    (TFLOP/s) and the MUFU rate (Gop/s) of the units the prediction passes use."""
+    r = AluPeaks()
+    _check(lib().bo_measure_alu_peaks(C.byref(r)))
+    return {f: getattr(r, f) for f, _ in AluPeaks._fields_ if f != "pad"}

@@ -135,11 +135,17 @@ void serve(bo_server* S) {
     std::vector<Request> reqs;
     {
       std::unique_lock<std::mutex> lk(S->mu);
+      // wake for requests, for a session to retire, or for a waiting session
+      // that now fits (a waiting session that does not fit wakes nobody)
       S->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] {
         if (S->stop) return true;
-        for (int64_t id : S->live)
-          if (!S->sessions[id].pending.empty()) return true;
-        return !S->waiting.empty();
+        for (int64_t id : S->live) {
+          const Session& ss = S->sessions[id];
+          if (!ss.pending.empty() || ss.closing) return true;
+        }
+        if (S->waiting.empty()) return false;
+        const Session& w = S->sessions[S->waiting.front()];
+        return (int)S->live.size() < S->cfg.max_sessions && S->bytes_in_use + w.est_bytes <= S->cfg.budget_bytes;
       });
       if (S->stop) break;
       retire_closed(S);

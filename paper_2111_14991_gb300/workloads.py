@@ -24,7 +24,7 @@ import numpy as np
 
 __all__ = [
     "Space", "Landscape", "config1_space", "config2_space", "config3_space",
-    "batched_spaces", "paper_shaped_space", "PAPER_SHAPED", "generic_space",
+    "batched_spaces", "batched_specs", "batched_space", "paper_shaped_space", "PAPER_SHAPED", "generic_space",
     "random_initial_sample", "clustered_observations",
 ]
 
@@ -210,18 +210,30 @@ def paper_shaped_space(kind: str, seed: int = 0) -> Space:
     return sp
 
 
-def batched_spaces(count: int = 256, seed: int = 0, n_min: int = 1000, n_max: int = 500_000):
-    """Uneven sessions: d ~ U{3..9}, N ~ log-uniform[n_min, n_max], n_obs ~ U{20..400}."""
+def batched_specs(count: int = 256, seed: int = 0, n_min: int = 1000, n_max: int = 500_000):
+    """(d, n_valid, n_obs) of each uneven session: d ~ U{3..9},
+    N ~ log-uniform[n_min, n_max], n_obs ~ U{20..400}."""
     rng = np.random.default_rng(seed + 4242)
     out = []
-    for s in range(count):
+    for _ in range(count):
         d = int(rng.integers(3, 10))
         n_valid = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
         n_obs = int(rng.integers(20, 401))
-        sp = generic_space(seed * 100003 + s, d, n_valid, name=f"batched-{s}")
-        sp.meta.update(n_obs=n_obs, session=s)
-        out.append(sp)
+        out.append((d, n_valid, n_obs))
     return out
+
+
+def batched_space(seed: int, s: int, spec) -> Space:
+    """Session s of the batched configuration with spec (d, n_valid, n_obs)."""
+    d, n_valid, n_obs = spec
+    sp = generic_space(seed * 100003 + s, d, n_valid, name=f"batched-{s}")
+    sp.meta.update(n_obs=n_obs, session=s)
+    return sp
+
+
+def batched_spaces(count: int = 256, seed: int = 0, n_min: int = 1000, n_max: int = 500_000):
+    """Uneven sessions: d ~ U{3..9}, N ~ log-uniform[n_min, n_max], n_obs ~ U{20..400}."""
+    return [batched_space(seed, s, spec) for s, spec in enumerate(batched_specs(count, seed, n_min, n_max))]
 
 
 # ---------------------------------------------------------------------------

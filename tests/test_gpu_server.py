@@ -107,3 +107,67 @@ def test_rejects_session_above_budget():
         srv.open(sp.grids, sp.invalid, precision="fp16x3", n_max=128)
     assert e.value.code == 6
     srv.close()
+
+
+def test_queued_session_admitted_when_memory_frees():
+    """Admission as memory frees up: under a budget that holds either of two
+    sessions but not both, the second waits (its requests stay pending) while
+    the first is served; closing the first admits the second, whose results
+    equal its alone twin's and the FP64 oracle's (Sec. III-A loop per request:
+    observe, then suggest)."""
+    import oracle as O
+    from paper_2111_14991_gb300 import Server, Space
+    from tolerances import REDUCED, pick_ok
+    a_sp = W.generic_space(41, 6, 24000)
+    b_sp = W.generic_space(42, 5, 20000)
+    data = []
+    for seed, sp in ((41, a_sp), (42, b_sp)):
+        land = W.Landscape(sp, seed)
+        idx = W.clustered_observations(land, 30, seed)
+        data.append((sp, idx, land.clean(idx)))
+    # each session's device bytes, measured alone
+    sizes = []
+    for sp, idx, y in data:
+        srv = Server(budget_bytes=1 << 40)
+        s = srv.open(sp.grids, sp.invalid, precision="fp16x3", n_max=64)
+        srv.submit(s, int(idx[0]), float(y[0]), tag=0)
+        drain(srv, 1)
+        sizes.append(srv.stats()["bytes_in_use"])
+        srv.close()
+    budget = int(max(sizes) * 1.25) + (256 << 10)     # the estimate adds at most 48 KB of tables
+    assert sum(sizes) > budget
+    srv = Server(budget_bytes=budget, max_sessions=8)
+    sa = srv.open(a_sp.grids, a_sp.invalid, precision="fp16x3", n_max=64)
+    sb = srv.open(b_sp.grids, b_sp.invalid, precision="fp16x3", n_max=64)
+    (_, ia, ya), (_, ib, yb) = data
+    for r in range(len(ia)):
+        srv.submit(sa, int(ia[r]), float(ya[r]), tag=r)
+    for r in range(len(ib)):
+        srv.submit(sb, int(ib[r]), float(yb[r]), tag=1000 + r)
+    got = drain(srv, len(ia))
+    assert sorted(c["tag"] for c in got) == list(range(len(ia)))
+    time.sleep(0.2)
+    assert srv.poll(wait_ms=50) == []                # B still waits for memory
+    st = srv.stats()
+    assert st["admitted"] == 1 and st["bytes_in_use"] <= budget
+    srv.close_session(sa)                            # A retires, B is admitted
+    got_b = {c["tag"] - 1000: c for c in drain(srv, len(ib))}
+    st = srv.stats()
+    assert st["admitted"] == 2 and st["closed"] >= 1 and st["bytes_in_use"] <= budget
+    srv.close()
+    twin = Space(b_sp.grids, b_sp.invalid, precision="fp16x3", n_max=64)
+    o = O.OracleSession(b_sp.grids, b_sp.invalid)
+    for r in range(len(ib)):
+        twin.observe(int(ib[r]), float(yb[r]))
+        o.observe(int(ib[r]), float(yb[r]))
+        ref = twin.suggest()
+        orc = o.suggest()
+        c = got_b[r]
+        assert c["status"] == 0 and c["observed"], c
+        assert c["idx"] == ref["idx"] or \
+            abs(c["info"]["score"] - ref["score"]) <= 1e-6 * max(abs(ref["score"]), 1), r
+        p = o.last_pass
+        assert pick_ok(p["scores"]["ei"], c["idx"], orc["idx"], **REDUCED), (r, c["idx"], orc["idx"])
+        assert abs(c["info"]["mu"] - p["mu"][c["idx"]]) <= 1e-3 * max(abs(p["mu"][c["idx"]]), 1.0)
+        assert abs(c["info"]["sigma"] - p["sigma"][c["idx"]]) <= 1e-3
+    twin.close()
