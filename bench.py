@@ -74,6 +74,11 @@ TRAFFIC = {
 }
 
 
+def log(msg):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def space_for(cfg):
     from paper_2111_14991_gb300 import workloads as W
     return {1: W.config1_space, 2: W.config2_space, 3: W.config3_space}[cfg]()
@@ -419,23 +424,37 @@ def measure_serving(count, rate, duration, precision, extra=160, seed=0, budget_
     configuration's sizes, for `duration` seconds; then a closed-loop run with
     one request of every session always in flight (saturation)."""
     from paper_2111_14991_gb300 import Server
+    t_gen = time.time()
     sess = session_inputs(count, "served", seed=seed, extra=extra)
+    t_gen = time.time() - t_gen
+    log(f"served: {count} sessions generated in {t_gen:.1f} s")
     srv = Server(budget_bytes=budget_gb << 30, max_sessions=count)
     rng = np.random.default_rng(seed + 99)
     sids, pending = [], []
     t_setup = time.time()
-    for x in sess:
-        sid = srv.open(x["grids"], x["invalid"], precision=precision, af="ei", n_max=512)
-        for i, v in zip(x["idx"], x["y"]):
-            srv.submit(sid, int(i), float(v), suggest=False)
-        sids.append(sid)
+    for x in sess:                               # every session opened (admitted) before any request
+        sids.append(srv.open(x["grids"], x["invalid"], precision=precision, af="ei", n_max=512))
         pending.append(list(zip(x["rest"].tolist(), x["y_rest"].tolist())))
-    n_warm = srv.stats()["requests"]
-    t_end = time.time() + 600
-    while srv.stats()["completed"] < n_warm and time.time() < t_end:
-        srv.poll(4096, wait_ms=20)
-    srv.poll(1 << 16, wait_ms=0)
+    # tags: initial observations WARM + k, open loop k, closed loop CLOSED + session
+    WARM, CLOSED = 1 << 40, 1 << 41
+    n_warm = 0
+    for sid, x in zip(sids, sess):
+        for i, v in zip(x["idx"], x["y"]):
+            srv.submit(sid, int(i), float(v), tag=WARM + n_warm, suggest=False)
+            n_warm += 1
+    t_end = time.time() + 300
+    errors, got = 0, 0
+    while got < n_warm and time.time() < t_end:
+        cs = srv.poll(1 << 14, wait_ms=20)
+        got += len(cs)
+        errors += sum(c["status"] != 0 for c in cs)
     t_setup = time.time() - t_setup
+    st = srv.stats()
+    log(f"served: initial observations {got}/{n_warm} in {t_setup:.1f} s, "
+        f"{st['iterations']} iterations, {errors} errors")
+    if got < n_warm:
+        srv.close()
+        return {"sessions": count, "error": f"initial observations incomplete after {t_setup:.0f} s"}
     sid_pos = {sid: k for k, sid in enumerate(sids)}
     # ---- open loop
     n_req = int(rate * duration)
@@ -454,10 +473,13 @@ def measure_serving(count, rate, duration, precision, extra=160, seed=0, budget_
     t_end = time.time() + 120
     while len(done) < submitted and time.time() < t_end:
         done += srv.poll(4096, wait_ms=20)
+    assert all(c["tag"] < WARM for c in done)
+    log(f"served: open loop {len(done)}/{submitted} completed")
     lat = np.array([c["t_done"] - c["t_submit"] for c in done if c["idx"] >= 0])
     span = max(c["t_done"] for c in done) - t0
     scored = sum(c["info"]["n_scored"] for c in done if c["idx"] >= 0)
-    open_loop = {"requests": len(lat), "rate_req_s": rate, "duration_s": round(span, 3),
+    open_loop = {"requests": len(lat), "errors": sum(c["status"] != 0 for c in done),
+                 "rate_req_s": rate, "duration_s": round(span, 3),
                  "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
                  "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
                  "candidates_per_s": round(scored / span, 1)}
@@ -468,25 +490,30 @@ def measure_serving(count, rate, duration, precision, extra=160, seed=0, budget_
     for s in range(count):
         if pending[s]:
             i, v = pending[s].pop()
-            srv.submit(sids[s], i, v, tag=s)
+            srv.submit(sids[s], i, v, tag=CLOSED + s)
             inflight += 1
-    scored, n_done, t_stop, lat_c = 0, 0, t0 + duration, []
-    while inflight and srv.now() < t_stop:
+    scored, n_done, t_stop, lat_c, errs_c = 0, 0, t0 + duration, [], 0
+    while inflight > 0 and srv.now() < t_stop:
         for c in srv.poll(4096, wait_ms=5):
+            assert c["tag"] >= CLOSED, c["tag"]
             inflight -= 1
             n_done += 1
+            errs_c += c["status"] != 0
             scored += c["info"]["n_scored"]
             lat_c.append(c["t_done"] - c["t_submit"])
             s = sid_pos[c["session"]]
             if pending[s]:
                 i, v = pending[s].pop()
-                srv.submit(sids[s], i, v, tag=s)
+                srv.submit(sids[s], i, v, tag=CLOSED + s)
                 inflight += 1
     span = srv.now() - t0
-    while inflight:
+    t_end = time.time() + 120
+    while inflight > 0 and time.time() < t_end:
         inflight -= len(srv.poll(4096, wait_ms=20))
     st = srv.stats()
-    closed_loop = {"requests": n_done, "duration_s": round(span, 3), "candidates_per_s": round(scored / span, 1),
+    log(f"served: closed loop {n_done} requests in {span:.1f} s")
+    closed_loop = {"requests": n_done, "errors": int(errs_c), "duration_s": round(span, 3),
+                   "candidates_per_s": round(scored / span, 1),
                    "iterations": st["iterations"] - it0["iterations"],
                    "p50_ms": round(1e3 * float(np.percentile(lat_c, 50)), 3) if lat_c else None,
                    "p99_ms": round(1e3 * float(np.percentile(lat_c, 99)), 3) if lat_c else None}
@@ -494,7 +521,8 @@ def measure_serving(count, rate, duration, precision, extra=160, seed=0, budget_
     srv.close()
     return {"sessions": count, "budget_gb": budget_gb, "candidates": sum(x["n_valid"] for x in sess),
             "open_loop": open_loop, "closed_loop": closed_loop, "admitted": stats["admitted"],
-            "bytes_in_use": stats["bytes_in_use"], "setup_s": round(t_setup, 1)}
+            "bytes_in_use": stats["bytes_in_use"], "setup_s": round(t_setup, 1),
+            "init_errors": int(errors)}
 
 
 def measure_latency(cfg_id, precision, reps, flush):
@@ -535,6 +563,7 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MB > 129 MB L2
     stream = torch.cuda.current_stream()
     measure_alu()
+    log(f"alu peaks {ALU}")
 
     with ClockSampler(dev) as clk:
         m = measure_device(args.config, args.precision, steps, warm, flush, stream)
@@ -582,6 +611,7 @@ def run_ours(args, rank, world):
             if (fcfg, fprec) == (args.config, args.precision):
                 continue
             f = measure_device(fcfg, fprec, steps if fprec != "fp64" or fcfg != 3 else 3, 3, flush, stream)
+            log(f"form config{fcfg}/{fprec}: {f['value']:.4g} candidates/s, kernel {1e3 * f['k1']:.3f} ms")
             form = {
                 "value": round(f["value"], 1), "unit": "candidates/s",
                 "ms_per_step": round(1e3 * sum(f["times"]) / len(f["times"]), 4),
@@ -601,6 +631,7 @@ def run_ours(args, rank, world):
         if not args.no_batched:
             bsteps = max(3, min(steps, 10))
             f = measure_batched(args.batch_sessions, bsteps, 3, "fp16x3", stream)
+            log(f"batched: {f['value']:.4g} candidates/s")
             peak = _peaks()["bf16_tflops"]
             ach = f["flops"] / sum(f["times"]) / 1e12
             forms["config4/fp16x3-batched"] = {
@@ -838,6 +869,7 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.config)
+            log("cpu baseline done")
         print(json.dumps(out))
 
 

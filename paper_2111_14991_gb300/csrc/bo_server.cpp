@@ -114,6 +114,10 @@ void retire_closed(bo_server* S) {
   for (size_t k = 0; k < S->live.size();) {
     Session& ss = S->sessions[S->live[k]];
     if (ss.closing && ss.pending.empty()) {
+      if (S->batch) {                      // the batch refers to the space (and may own memory through it)
+        bo_batch_destroy(S->batch);
+        S->batch = nullptr;
+      }
       S->bytes_in_use -= space_bytes(ss.space);
       bo_space_destroy(ss.space);
       ss.space = nullptr;
@@ -150,13 +154,18 @@ void serve(bo_server* S) {
       if (S->stop) break;
       retire_closed(S);
       admit(S);
-      if (S->batch_stale) {
+      bool work = false;
+      for (int64_t id : S->live) work = work || !S->sessions[id].pending.empty();
+      // the batch is rebuilt only when requests need it, so that a burst of
+      // admissions costs one rebuild
+      int batch_rc = BO_OK;
+      if (work && S->batch_stale) {
         if (S->batch) bo_batch_destroy(S->batch);
         S->batch = nullptr;
         spaces.clear();
         for (int64_t id : S->live) spaces.push_back(S->sessions[id].space);
-        if (!spaces.empty()) bo_batch_create(spaces.data(), (int32_t)spaces.size(), &S->batch);
-        S->batch_stale = false;
+        if (!spaces.empty()) batch_rc = bo_batch_create(spaces.data(), (int32_t)spaces.size(), &S->batch);
+        S->batch_stale = S->batch == nullptr;
       }
       for (size_t k = 0; k < S->live.size(); ++k) {
         Session& ss = S->sessions[S->live[k]];
@@ -166,9 +175,23 @@ void serve(bo_server* S) {
           ss.pending.pop_front();
         }
       }
+      if (!take.empty() && !S->batch) {    // no batch to run them on: each request fails
+        for (size_t q = 0; q < take.size(); ++q) {
+          bo_completion c{};
+          c.tag = reqs[q].tag;
+          c.session = S->live[take[q]];
+          c.status = batch_rc != BO_OK ? batch_rc : BO_ERR_CUDA;
+          c.idx = -1;
+          c.t_submit = reqs[q].t_submit;
+          c.t_done = now_s(S);
+          ++S->stats.completed;
+          S->done.push_back(c);
+        }
+        take.clear();
+      }
       S->cv_done.notify_all();             // admissions / rejections may have produced completions
     }
-    if (take.empty() || !S->batch) continue;
+    if (take.empty()) continue;
     const double t_start = now_s(S);
     const size_t n = spaces.size();
     std::vector<int64_t> idx(n, -1), out_idx(n, -1);
