@@ -25,10 +25,13 @@
  *   - All device work of a space is ordered on the stream given at creation.
  *     A space may be used by one host thread at a time.
  *   - Environment, read when a space / batch is created: BO_NO_COOP (set:
- *     a space's observation update runs as six phase launches instead of one
- *     cooperative launch) and BO_NO_GRAPH (set: a batch launches its kernels
- *     one by one instead of replaying a captured CUDA graph).  Results are the
- *     same up to the reduction order of the update's pivot.
+ *     a space's observation update runs as four phase launches instead of one
+ *     cooperative launch), BO_FUSED_ACQ (set: a reduced-precision space's
+ *     prediction pass carries the acquisition as its tail, one cooperative
+ *     launch instead of two; the same results) and BO_NO_GRAPH (set: a batch
+ *     launches its kernels one by one instead of replaying a captured CUDA
+ *     graph).  Results are the same up to the reduction order of the
+ *     update's pivot.
  */
 #ifndef BO_SUGGEST_H
 #define BO_SUGGEST_H

@@ -43,7 +43,8 @@ def _compile(src: str, obj: str, extra):
 def build(verbose: bool = False, force: bool = False, extra=()) -> str:
     os.makedirs(OUT, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    headers = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+               glob.glob(os.path.join(ROOT, "include", "*.h")))
     newest_header = max(os.path.getmtime(h) for h in headers)
     jobs = []
     objs = []

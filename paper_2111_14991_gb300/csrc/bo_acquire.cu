@@ -11,6 +11,7 @@
 #include <cfloat>
 #include <climits>
 
+#include "bo_acquire_dev.cuh"
 #include "bo_internal.h"
 
 namespace bo {
@@ -109,98 +110,20 @@ __device__ __forceinline__ void scores3(T mu, T sigma, T fplus, T lam, bool need
 }
 
 // ---- FP32 posteriors: (score, index) packed into one 64-bit key ----------
-// The high word maps the float score onto unsigned integers in the same
-// order (negative values bit-inverted, positive ones with the sign bit set;
-// -0 is first made +0), the low word holds 2^32 - 1 - index, so a larger key
-// is a higher score, then a lower index: the selection order of better().
-// Key 0 is "no candidate" (it would need a NaN score, which never enters).
-// Indices must stay below 2^32 - 1.
-__device__ __forceinline__ unsigned long long pack_key(float s, long long i) {
-  uint32_t u = __float_as_uint(s + 0.0f);
-  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-  return ((unsigned long long)u << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)i);
-}
-__device__ __forceinline__ float key_score(unsigned long long k) {
-  const uint32_t u = (uint32_t)(k >> 32);
-  return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
-}
-__device__ __forceinline__ long long key_idx(unsigned long long k) {
-  return (long long)(0xFFFFFFFFu - (uint32_t)k);
-}
-
-// keep the three largest keys, t[0] >= t[1] >= t[2] (real keys are distinct)
-__device__ __forceinline__ void key_insert(unsigned long long (&t)[kMaxK], unsigned long long k) {
-  if (k <= t[2]) return;
-  if (k > t[0]) {
-    t[2] = t[1]; t[1] = t[0]; t[0] = k;
-  } else if (k > t[1]) {
-    t[2] = t[1]; t[1] = k;
-  } else {
-    t[2] = k;
-  }
-}
-
-// The three largest keys of the lanes' sorted lists, returned in every lane:
-// three rounds of a warp maximum, the lane holding it popping its head.
-__device__ __forceinline__ void warp_top3(unsigned long long (&t)[kMaxK]) {
-  unsigned long long out[kMaxK];
-#pragma unroll
-  for (int r = 0; r < kMaxK; ++r) {
-    unsigned long long m = t[0];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
-      m = x > m ? x : m;
-    }
-    out[r] = m;
-    if (m != 0ull && t[0] == m) { t[0] = t[1]; t[1] = t[2]; t[2] = 0ull; }
-  }
-#pragma unroll
-  for (int r = 0; r < kMaxK; ++r) t[r] = out[r];
-}
-
-// Block-wide top-3 per AF: each warp's three keys through shared memory,
-// then warp 0 takes the three largest of them.  Every thread calls it; the
-// result is valid in warp 0.
-__device__ __forceinline__ void block_top3(unsigned long long (&t)[3][kMaxK],
-                                           unsigned long long (*s_key)[3][kMaxK]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) warp_top3(t[q]);
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-#pragma unroll
-      for (int r = 0; r < kMaxK; ++r) s_key[warp][q][r] = t[q][r];
-  __syncthreads();
-  if (warp == 0) {
-    constexpr int kWarps = kThreads / 32;
-    static_assert(kWarps * kMaxK <= 32, "one key per lane");
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      t[q][0] = lane < kWarps * kMaxK ? s_key[lane / kMaxK][q][lane % kMaxK] : 0ull;
-      t[q][1] = t[q][2] = 0ull;
-      warp_top3(t[q]);
-    }
-  }
-}
-
-// acquire_body for FP32 posteriors: the same scores in the same FP32
-// arithmetic (EI and PI share z and Phi), kept as packed keys; block
-// partials are keys (in TopEntry::idx), merged by the last block.
+// (bo_acquire_dev.cuh: the key order is the selection order of better()).
+// acquire_body_f32: the scores in FP32 (EI and PI share z and Phi), kept as
+// packed keys; block partials are keys (in TopEntry::idx), merged by the last
+// block.
 __device__ __forceinline__ void acquire_body_f32(const AcqDev& v, const PassArgs& a, const int block,
                                                  const int nblocks, const double sum_var) {
   __shared__ unsigned long long s_key[kThreads / 32][3][kMaxK];
   __shared__ bool s_last;
+  __shared__ double s_lam[3];   // FP64 scalars formed once per block and broadcast
   const float* mu = static_cast<const float*>(v.mu);
   const float* var = static_cast<const float*>(v.var);
-
-  const double mean_var = a.n_unvisited > 0 ? sum_var / (double)a.n_unvisited : 0.0;
-  const double var_s = a.first_pass ? mean_var : *v.var_s;
-  double lam = a.lambda_const;
-  if (a.explore == BO_EXPLORE_CV)
-    lam = var_s > 0.0 ? (mean_var / (a.mu_s_raw / a.fplus_raw)) / var_s : 0.0;
+  if (threadIdx.x == 0) acq::pass_lambda(a, sum_var, a.first_pass ? 0.0 : *v.var_s, &s_lam[0], &s_lam[1], &s_lam[2]);
+  __syncthreads();
+  const double mean_var = s_lam[0], var_s = s_lam[1], lam = s_lam[2];
   const float lamT = (float)lam, fpT = (float)a.fplus_t;
   const int n_af = a.n_af;
   const int af0 = a.af[0], af1 = a.af[1], af2 = a.af[2];
@@ -213,33 +136,9 @@ __device__ __forceinline__ void acquire_body_f32(const AcqDev& v, const PassArgs
   const int64_t stride = (int64_t)nblocks * kThreads;
   for (int64_t i = (int64_t)block * kThreads + threadIdx.x; i < v.N; i += stride) {
     if ((v.visited[i >> 5] >> (i & 31)) & 1u) continue;
-    const float m = mu[i];
-    const float vv = var[i];
-    const float sg = sqrtf(vv > 0.0f ? vv : 0.0f);
-    const float delta = fpT - m - lamT;
-    const float lcb = lamT * sg - m;
-    float ei, pi;
-    if (!(sg > 0.0f)) {
-      ei = delta > 0.0f ? delta : 0.0f;
-      pi = delta > 0.0f ? 1.0f : 0.0f;
-    } else {
-      const float z = delta / sg;
-      const float Phi = 0.5f * erfcf(-z * 0.70710678118654752440f);
-      const float phi = expf(-0.5f * z * z) * 0.39894228040143267794f;
-      pi = Phi;
-      ei = delta * Phi + sg * phi;
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (q < n_af) {
-        const int af = q == 0 ? af0 : q == 1 ? af1 : af2;
-        float x = af == kEI ? ei : af == kPI ? pi : lcb;
-        if (!(x == x)) x = -FLT_MAX / 2.0f;   // NaN never wins
-        key_insert(top[q], pack_key(x, (long long)i));
-      }
-    }
+    acq::score_f32(mu[i], var[i], fpT, lamT, n_af, af0, af1, af2, (long long)i, top);
   }
-  block_top3(top, s_key);
+  acq::block_top3(top, &s_key[0][0][0], kThreads / 32);
   if (threadIdx.x < 32 && threadIdx.x < 3 * kMaxK) {
     const int q = threadIdx.x / kMaxK, r = threadIdx.x % kMaxK;
     unsigned long long k = 0ull;
@@ -249,7 +148,7 @@ __device__ __forceinline__ void acquire_body_f32(const AcqDev& v, const PassArgs
       for (int rr = 0; rr < kMaxK; ++rr)
         if (qq == q && rr == r) k = top[qq][rr];
     TopEntry* out = v.partial + ((size_t)block * 3 + q) * kMaxK + r;
-    out->score = (double)key_score(k);
+    out->score = (double)acq::key_score(k);
     out->idx = (long long)k;
     __threadfence();
   }
@@ -273,34 +172,12 @@ __device__ __forceinline__ void acquire_body_f32(const AcqDev& v, const PassArgs
     for (int q = 0; q < 3; ++q)
 #pragma unroll
       for (int r = 0; r < kMaxK; ++r)
-        key_insert(top[q], (unsigned long long)__ldcg(&v.partial[((size_t)b * 3 + q) * kMaxK + r].idx));
-  block_top3(top, s_key);
-  if (threadIdx.x < 3) {
-    const int q = threadIdx.x;
-    unsigned long long t[kMaxK];
-#pragma unroll
-    for (int r = 0; r < kMaxK; ++r) t[r] = q == 0 ? top[0][r] : q == 1 ? top[1][r] : top[2][r];
-    bo_pass_result* res = v.result;
-    for (int r = 0; r < 3; ++r) {
-      const bool ok = q < a.n_af && r < a.k && t[r] != 0ull;
-      const long long i = ok ? key_idx(t[r]) : 0;
-      res->top_idx[q][r] = ok ? i : -1;
-      res->top_score[q][r] = ok ? (double)key_score(t[r]) : 0.0;
-      res->top_mu[q][r] = ok ? (double)mu[i] : 0.0;
-      const double vr = ok ? (double)var[i] : 0.0;
-      res->top_sigma[q][r] = ok ? sqrt(vr > 0.0 ? vr : 0.0) : 0.0;
-    }
-  }
+        acq::key_insert(top[q], (unsigned long long)__ldcg(&v.partial[((size_t)b * 3 + q) * kMaxK + r].idx));
+  acq::block_top3(top, &s_key[0][0][0], kThreads / 32);
+  if (threadIdx.x < 32)
+    acq::write_result_f32(v.result, top, a, mu, var, v.status_in ? *v.status_in : BO_OK, sum_var, mean_var, lam,
+                          var_s);
   if (threadIdx.x == 0) {
-    bo_pass_result* res = v.result;
-    res->status = v.status_in ? *v.status_in : BO_OK;
-    if (res->status == BO_OK && !(mean_var == mean_var)) res->status = BO_ERR_NUMERIC;
-    res->n_fit = a.n;
-    res->n_scored = a.n_unvisited;
-    res->sum_var = sum_var;
-    res->mean_var = mean_var;
-    res->lambda = lam;
-    res->mean_var_s = var_s;
     if (a.first_pass) *v.var_s = mean_var;
     *v.counter = 0;
   }
@@ -317,12 +194,12 @@ __device__ __forceinline__ void acquire_body(const AcqDev& v, const PassArgs& a,
   const T* mu = static_cast<const T*>(v.mu);
   const T* var = static_cast<const T*>(v.var);
 
-  // lambda from the pass's mean variance (every block computes the same value)
-  const double mean_var = a.n_unvisited > 0 ? sum_var / (double)a.n_unvisited : 0.0;
-  const double var_s = a.first_pass ? mean_var : *v.var_s;
-  double lam = a.lambda_const;
-  if (a.explore == BO_EXPLORE_CV)
-    lam = var_s > 0.0 ? (mean_var / (a.mu_s_raw / a.fplus_raw)) / var_s : 0.0;
+  // lambda from the pass's mean variance (every block computes the same value,
+  // one thread per block: FP64 scalars are broadcast, not repeated per thread)
+  __shared__ double s_lam[3];
+  if (threadIdx.x == 0) acq::pass_lambda(a, sum_var, a.first_pass ? 0.0 : *v.var_s, &s_lam[0], &s_lam[1], &s_lam[2]);
+  __syncthreads();
+  const double mean_var = s_lam[0], var_s = s_lam[1], lam = s_lam[2];
   const T lamT = (T)lam, fpT = (T)a.fplus_t;
 
   bool need_phi = false;
@@ -433,9 +310,15 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) acquire_batch_kernel(const AcqItem* items, const int* block_item,
                                                                  const int* block_local, const double* seg_part) {
   const AcqItem& it = items[block_item[blockIdx.x]];
-  double sum_var = 0.0;
-  for (int g = it.seg0; g < it.seg1; ++g)
-    for (int e = 0; e < 4; ++e) sum_var += seg_part[(size_t)g * 4 + e];
+  __shared__ double s_sum;        // formed once per block (FP64 is narrow on this GPU) and broadcast
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int g = it.seg0; g < it.seg1; ++g)
+      for (int e = 0; e < 4; ++e) t += seg_part[(size_t)g * 4 + e];
+    s_sum = t;
+  }
+  __syncthreads();
+  const double sum_var = s_sum;
   if constexpr (sizeof(T) == 4)
     acquire_body_f32(it.dev, it.args, block_local[blockIdx.x], it.nblocks, sum_var);
   else

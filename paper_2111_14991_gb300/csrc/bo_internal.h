@@ -68,6 +68,10 @@ struct DevView {
   double* y;                 // [n_max] raw fitted values
   double* linv;              // [n_max][n_max] L^-1, row-major, lower triangular
   double* beta;              // [n_max] L^-1 y~
+  double* uvec;              // [n_max] L^-1 (y - y0), y0 = y[0] (beta is affine in the mean of y)
+  double* evec;              // [n_max] L^-1 1
+  double* avec;              // [n_max] K^-1 (y - y0) (tensor-core forms: alpha = K^-1 y~)
+  double* bvec;              // [n_max] K^-1 1
   uint8_t* lsplit_hi;        // reduced-precision chunked copy of L^-1 (hi part, or the single tf32)
   uint8_t* lsplit_lo;        // (lo part; unused for the single tf32 form)
 
@@ -115,6 +119,37 @@ inline bool ensure_dynamic_smem(const void* kernel, size_t (&configured)[kMaxDev
   configured[dev] = bytes;
   return true;
 }
+
+#ifdef __CUDACC__
+// Sum of count per-block partials (written by other blocks, made visible by
+// the caller's fence / counter protocol), by every thread of a block: each
+// thread adds its strided share in order, a fixed warp butterfly and a
+// fixed-order sum of the warp results by one thread follow, so the value is
+// the same in every run.  Loads go to L2 in parallel instead of one dependent
+// chain.  (FP64 issues at 1/64 of the FP32 rate on this GPU: the scalar tail
+// runs in one thread and is broadcast, not repeated by every thread.)  red:
+// shared memory for blockDim.x / 32 + 1 doubles.  Every thread of the block
+// must call it; every thread gets the sum.
+__device__ __forceinline__ double block_sum_partials(const double* p, int count, double* red) {
+  double t = 0.0;
+  for (int b = threadIdx.x; b < count; b += blockDim.x) t += __ldcg(p + b);
+  if ((int)(threadIdx.x & ~31u) < count)           // warps without partials add nothing
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  const int nw = (int)(blockDim.x >> 5);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    red[nw] = s;
+  }
+  __syncthreads();
+  const double s = red[nw];
+  __syncthreads();
+  return s;
+}
+#endif
 
 // Scalars of one prediction pass known to the host.
 struct PassArgs {
@@ -221,6 +256,10 @@ int launch_observe_batch(const ObsItem* items, int count, const ObsBlock* blocks
                          const VisitItem* visits, int n_visits, bool tc, cudaStream_t s);
 int launch_predict_f64(const DevView& v, int n, int64_t n_unvisited, cudaStream_t s);
 int launch_predict_tc(const DevView& v, int n, int64_t n_unvisited, cudaStream_t s);
+// The tensor-core pass with the acquisition of `a` as its tail (one
+// cooperative launch writing the pass result); -2 if the device does not
+// launch it cooperatively (then predict + acquire as two launches).
+int launch_predict_acquire_tc(const DevView& v, int n, const PassArgs& a, cudaStream_t s);
 TcSess tc_session(const DevView& v, int n);
 int tc_dim_bucket(int d);
 // Cost-balanced segments of `count` spaces over `grid` CTAs; returns the segment count.

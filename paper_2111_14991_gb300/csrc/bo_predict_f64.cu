@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
   int* meta = reinterpret_cast<int*>(Ts + (TAB ? v.sqd_total : 0));
   uint8_t* Xc = reinterpret_cast<uint8_t*>(meta + 2 * d + 1);
   uint8_t* Cc = Xc + d * n_pad;
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kThreads / 32 + 1];
   __shared__ bool s_last;
 
   const int tid = threadIdx.x;
@@ -214,9 +214,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
   __syncthreads();
   if (s_last) {
     __threadfence();
+    const double t = block_sum_partials(v.partial, (int)gridDim.x, red);
     if (tid == 0) {
-      double t = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)v.partial)[b];
       v.stats->sum_var = t;
       v.stats->k1_done = 0;
     }

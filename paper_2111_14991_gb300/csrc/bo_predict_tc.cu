@@ -59,6 +59,7 @@
 #include <mutex>
 #include <vector>
 
+#include "bo_acquire_dev.cuh"
 #include "bo_internal.h"
 
 namespace bo {
@@ -99,6 +100,13 @@ struct TcParams {
   // b_slots fixed-size slots, or every piece of the space resident (loaded once)
   int b_resident, b_slots;
   size_t off_b, b_slot_bytes, off_x, x_buf_bytes, off_mu, off_bar;
+  // acquisition tail (one space, cooperative launch): after a grid barrier on
+  // the variance partials every CTA scores the candidates of its own tiles
+  int acq;
+  PassArgs args;
+  bo_pass_result* result;
+  TopEntry* acq_partial;     // [grid][3][3] per-CTA top-3 keys (in TopEntry::idx)
+  double* var_s;             // contextual-variance baseline
 };
 
 // Position in a CTA's work: one space with strided tiles, or a segment list.
@@ -452,6 +460,103 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
                : "memory");
+}
+
+// Acquisition tail of a single-space pass (the kernel is launched
+// cooperatively, so every CTA is resident): each CTA publishes its variance
+// partial and waits, bounded in time, until all have; every CTA then forms
+// the same variance sum (fixed order) and lambda, scores the candidates of its
+// own tiles (FP32, bo_acquire_dev.cuh) into a block top-3 per AF, and the last
+// CTA to finish merges the per-CTA lists into the pass result.  keys: shared
+// memory for [24 warps][3][3] keys (the A stages, free by now).
+__device__ __noinline__ void acquisition_tail(const TcParams& P, double my_vsum, unsigned long long* keys) {
+  __shared__ double s_sum;
+  __shared__ int s_ok;
+  __shared__ bool s_last;
+  const TcSess& S = P.s0;
+  const int G = (int)gridDim.x;
+  DevStats* st = P.stats;
+  if (threadIdx.x == 0) {
+    P.partial[blockIdx.x] = my_vsum;
+    __threadfence();
+    atomicAdd(&st->k1_done, 1u);
+    const unsigned long long t0 = now_ns();
+    int ok = 1;
+    while (*(volatile unsigned int*)&st->k1_done < (unsigned int)G) {
+      if (now_ns() - t0 > kWaitNs) {
+        atomicExch(P.status, BO_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  {
+    const double t = block_sum_partials(P.partial, G, reinterpret_cast<double*>(keys));
+    if (threadIdx.x == 0) s_sum = s_ok ? t : 0.0;
+  }
+  __syncthreads();
+  const PassArgs& a = P.args;
+  __shared__ double s_lam[3];   // mean_var, var_s, lambda: FP64 scalars, formed once and broadcast
+  if (threadIdx.x == 0) acq::pass_lambda(a, s_sum, a.first_pass ? 0.0 : *P.var_s, &s_lam[0], &s_lam[1], &s_lam[2]);
+  __syncthreads();
+  const double mean_var = s_lam[0], var_s = s_lam[1], lam = s_lam[2];
+  unsigned long long top[3][acq::kTop];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int r = 0; r < acq::kTop; ++r) top[q][r] = 0ull;
+  if (s_ok) {
+    const float lamT = (float)lam, fpT = (float)a.fplus_t;
+    const int my_tiles = blockIdx.x < S.num_tiles ? (S.num_tiles - 1 - (int)blockIdx.x) / G + 1 : 0;
+    for (int k = threadIdx.x; k < my_tiles * kRows; k += kThreads) {
+      const int64_t i = (int64_t)(blockIdx.x + (k / kRows) * G) * kRows + (k % kRows);
+      if (i >= S.N || ((S.visited[i >> 5] >> (i & 31)) & 1u)) continue;
+      acq::score_f32(S.mu[i], S.var[i], fpT, lamT, a.n_af, a.af[0], a.af[1], a.af[2], (long long)i, top);
+    }
+  }
+  acq::block_top3(top, keys, kThreads / 32);
+  if (threadIdx.x < 3 * acq::kTop) {
+    const int q = threadIdx.x / acq::kTop, r = threadIdx.x % acq::kTop;
+    unsigned long long k = 0ull;
+#pragma unroll
+    for (int qq = 0; qq < 3; ++qq)
+#pragma unroll
+      for (int rr = 0; rr < acq::kTop; ++rr)
+        if (qq == q && rr == r) k = top[qq][rr];
+    P.acq_partial[((size_t)blockIdx.x * 3 + q) * acq::kTop + r].idx = (long long)k;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->k2_done, 1u) == (unsigned int)G - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last CTA: every CTA's lists, merged (the key order is total: any merge order gives the same result)
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int r = 0; r < acq::kTop; ++r) top[q][r] = 0ull;
+  for (int b = threadIdx.x; b < G; b += kThreads)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int r = 0; r < acq::kTop; ++r)
+        acq::key_insert(top[q],
+                        (unsigned long long)__ldcg(&P.acq_partial[((size_t)b * 3 + q) * acq::kTop + r].idx));
+  acq::block_top3(top, keys, kThreads / 32);
+  if (threadIdx.x < 32)
+    acq::write_result_f32(P.result, top, a, S.mu, S.var, *(volatile int32_t*)P.status, s_sum, mean_var, lam,
+                          var_s);
+  if (threadIdx.x == 0) {
+    if (a.first_pass) *P.var_s = mean_var;
+    st->sum_var = s_sum;
+    st->k1_done = 0;
+    st->k2_done = 0;
+  }
 }
 
 template <int MODE, int DMAX, bool NU52>
@@ -1002,6 +1107,10 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
                  "r"(P.tmem_cols * P.acc_stages) : "memory");
   }
   if (P.batch) return;
+  if (P.acq) {
+    acquisition_tail(P, red[0] + red[1] + red[2] + red[3], reinterpret_cast<unsigned long long*>(smem));
+    return;
+  }
   if (threadIdx.x == 0) {
     P.partial[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
     __threadfence();
@@ -1009,12 +1118,13 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     s_last = (done == gridDim.x - 1);
   }
   __syncthreads();
-  if (s_last && threadIdx.x == 0) {
+  if (s_last) {
     __threadfence();
-    double t = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)P.partial)[b];
-    P.stats->sum_var = t;
-    P.stats->k1_done = 0;
+    const double t = block_sum_partials(P.partial, (int)gridDim.x, reinterpret_cast<double*>(smem));
+    if (threadIdx.x == 0) {
+      P.stats->sum_var = t;
+      P.stats->k1_done = 0;
+    }
   }
 }
 
@@ -1034,39 +1144,51 @@ TcShape shape_for(int precision, double nu, int dmax, int n_pad, bool batched) {
   return it == g_tuned.end() ? TcShape{} : it->second;
 }
 
+// Launch one instantiation; cooperative launches (the acquisition tail's grid
+// barrier needs every CTA resident) return -2 when the device refuses them.
 template <int MODE, int DMAX, bool NU52>
-int launch_mode(const TcParams& P, size_t smem, int grid, cudaStream_t s) {
+int launch_mode(const TcParams& P, size_t smem, int grid, bool coop, cudaStream_t s) {
   static size_t configured[kMaxDevices] = {};
   if (!ensure_dynamic_smem((const void*)predict_tc_kernel<MODE, DMAX, NU52>, configured, smem)) return -1;
+  if (coop) {
+    void* args[] = {const_cast<TcParams*>(&P)};
+    if (cudaLaunchCooperativeKernel((const void*)predict_tc_kernel<MODE, DMAX, NU52>, dim3(grid), dim3(kThreads),
+                                    args, smem, s) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return -2;
+    }
+    return 1;
+  }
   predict_tc_kernel<MODE, DMAX, NU52><<<grid, kThreads, smem, s>>>(P);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <int MODE, bool NU52>
-int launch_dims(const TcParams& P, int dmax, size_t smem, int grid, cudaStream_t s) {
+int launch_dims(const TcParams& P, int dmax, size_t smem, int grid, bool coop, cudaStream_t s) {
   switch (dmax) {
-    case 4: return launch_mode<MODE, 4, NU52>(P, smem, grid, s);
-    case 7: return launch_mode<MODE, 7, NU52>(P, smem, grid, s);
-    case 9: return launch_mode<MODE, 9, NU52>(P, smem, grid, s);
-    default: return launch_mode<MODE, 16, NU52>(P, smem, grid, s);
+    case 4: return launch_mode<MODE, 4, NU52>(P, smem, grid, coop, s);
+    case 7: return launch_mode<MODE, 7, NU52>(P, smem, grid, coop, s);
+    case 9: return launch_mode<MODE, 9, NU52>(P, smem, grid, coop, s);
+    default: return launch_mode<MODE, 16, NU52>(P, smem, grid, coop, s);
   }
 }
 
-int dispatch(const TcParams& P, int precision, double nu, int dmax, size_t smem, int grid, cudaStream_t s) {
+int dispatch(const TcParams& P, int precision, double nu, int dmax, size_t smem, int grid, cudaStream_t s,
+             bool coop = false) {
   const bool nu52 = nu == 2.5;
   switch (precision) {
     case BO_PREC_FP16X3:
-      return nu52 ? launch_dims<BO_PREC_FP16X3, true>(P, dmax, smem, grid, s)
-                  : launch_dims<BO_PREC_FP16X3, false>(P, dmax, smem, grid, s);
+      return nu52 ? launch_dims<BO_PREC_FP16X3, true>(P, dmax, smem, grid, coop, s)
+                  : launch_dims<BO_PREC_FP16X3, false>(P, dmax, smem, grid, coop, s);
     case BO_PREC_BF16X3:
-      return nu52 ? launch_dims<BO_PREC_BF16X3, true>(P, dmax, smem, grid, s)
-                  : launch_dims<BO_PREC_BF16X3, false>(P, dmax, smem, grid, s);
+      return nu52 ? launch_dims<BO_PREC_BF16X3, true>(P, dmax, smem, grid, coop, s)
+                  : launch_dims<BO_PREC_BF16X3, false>(P, dmax, smem, grid, coop, s);
     case BO_PREC_TF32X3:
-      return nu52 ? launch_dims<BO_PREC_TF32X3, true>(P, dmax, smem, grid, s)
-                  : launch_dims<BO_PREC_TF32X3, false>(P, dmax, smem, grid, s);
+      return nu52 ? launch_dims<BO_PREC_TF32X3, true>(P, dmax, smem, grid, coop, s)
+                  : launch_dims<BO_PREC_TF32X3, false>(P, dmax, smem, grid, coop, s);
     case BO_PREC_TF32:
-      return nu52 ? launch_dims<BO_PREC_TF32, true>(P, dmax, smem, grid, s)
-                  : launch_dims<BO_PREC_TF32, false>(P, dmax, smem, grid, s);
+      return nu52 ? launch_dims<BO_PREC_TF32, true>(P, dmax, smem, grid, coop, s)
+                  : launch_dims<BO_PREC_TF32, false>(P, dmax, smem, grid, coop, s);
     default:
       return -1;
   }
@@ -1169,7 +1291,9 @@ TcSess tc_session(const DevView& v, int n) {
   return S;
 }
 
-int launch_predict_tc(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStream_t s) {
+namespace {
+
+int launch_single(const DevView& v, int n, const PassArgs* a, cudaStream_t s) {
   if (n < 1 || n > v.n_max || v.precision == BO_PREC_FP64 || v.d > 16) return -1;
   TcParams P{};
   P.s0 = tc_session(v, n);
@@ -1185,7 +1309,25 @@ int launch_predict_tc(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStre
   if (!smem) return -1;
   const int grid = std::min(P.s0.num_tiles, num_sms());
   if (grid > v.max_partials) return -1;
-  return dispatch(P, v.precision, v.nu, dmax, smem, grid, s);
+  if (a) {
+    if (grid > v.max_acq_blocks || a->result_slot < 0 || a->result_slot >= v.max_results) return -1;
+    P.acq = 1;
+    P.args = *a;
+    P.result = v.results + a->result_slot;
+    P.acq_partial = v.acq_partial;
+    P.var_s = &v.stats->var_s;
+  }
+  return dispatch(P, v.precision, v.nu, dmax, smem, grid, s, a != nullptr);
+}
+
+}  // namespace
+
+int launch_predict_tc(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStream_t s) {
+  return launch_single(v, n, nullptr, s);
+}
+
+int launch_predict_acquire_tc(const DevView& v, int n, const PassArgs& a, cudaStream_t s) {
+  return launch_single(v, n, &a, s);
 }
 
 int tc_plan_batch(const TcSess* sess, int count, int dmax, int grid, std::vector<TcSeg>* segs,

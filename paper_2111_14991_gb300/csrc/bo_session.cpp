@@ -2,7 +2,7 @@
 // observation bookkeeping and the selection of acquisition functions.
 //
 // Device work per call:
-//   bo_observe  -> observation update of L^-1 and beta (FP64), or a visited bit
+//   bo_observe  -> observation update of L^-1, beta and alpha (FP64), or a visited bit
 //   bo_suggest  -> prediction pass (K* tiles + contraction + row reduction),
 //                  then acquisition + masked top-k, then one small copy back
 #include <algorithm>
@@ -78,8 +78,9 @@ size_t space_device_bytes(int d, int64_t N, int n_max, int precision, int num_sm
   const size_t fsz = precision == BO_PREC_FP64 ? 8 : 4;
   size_t t = r(d * N_pad) + r(d * 256 * 8) + r(d * 256 * 4) + r((N_pad / 32 + 1) * 4);
   t += r(n * d * 8) + r(n * d) + r(kSqdMaxBytes) + r((2 * BO_MAX_PARAMS + 1) * 4);
-  t += r(n * 8) + r(n * n * 8) + r(n * 8);
+  t += r(n * 8) + r(n * n * 8) + r(n * 8) + 2 * r(n * 8);
   if (precision != BO_PREC_FP64) {
+    t += 2 * r(n * 8);
     t += r((size_t)(tc_dim_bucket(d) + 2) * n * 4);
     t += split_parts(precision) * r(lsplit_bytes((int)n, precision));
   }
@@ -189,6 +190,15 @@ int launch_pass(bo_space* s, const std::vector<int>& afs, int slot) {
   PassArgs a;
   const int rc = prepare_pass(s, afs, slot, &a);
   if (rc != BO_OK) return rc;
+  if (s->desc.precision != BO_PREC_FP64 && s->fused_acquire) {
+    const int k = launch_predict_acquire_tc(s->v, s->n_fit, a, s->stream);
+    if (k > 0) {
+      s->launches += k;
+      return BO_OK;
+    }
+    if (k != -2) return fail(BO_ERR_CUDA, "prediction launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    s->fused_acquire = false;      // not launchable cooperatively here: two launches from now on
+  }
   const int k1 = s->desc.precision == BO_PREC_FP64
                      ? launch_predict_f64(s->v, s->n_fit, a.n_unvisited, s->stream)
                      : launch_predict_tc(s->v, s->n_fit, a.n_unvisited, s->stream);
@@ -420,6 +430,7 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   s->n_cap = D.n_max;
   s->rng = D.seed;
   s->coop_update = getenv("BO_NO_COOP") == nullptr;
+  s->fused_acquire = getenv("BO_FUSED_ACQ") != nullptr;
   s->sel.init(D.af, D.skip_threshold, D.discount, D.rif);
   for (int p = 0; p < D.d; ++p) {
     s->sizes.push_back(D.n_values[p]);
@@ -505,6 +516,12 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   TRY(dalloc_n(s, (size_t)n_alloc, &v.y));
   TRY(dalloc_n(s, (size_t)n_alloc * n_alloc, &v.linv));
   TRY(dalloc_n(s, (size_t)n_alloc, &v.beta));
+  TRY(dalloc_n(s, (size_t)n_alloc, &v.uvec));
+  TRY(dalloc_n(s, (size_t)n_alloc, &v.evec));
+  if (D.precision != BO_PREC_FP64) {
+    TRY(dalloc_n(s, (size_t)n_alloc, &v.avec));
+    TRY(dalloc_n(s, (size_t)n_alloc, &v.bvec));
+  }
   if (D.precision != BO_PREC_FP64) {
     TRY(dalloc_n(s, lsplit_bytes(n_alloc, D.precision), &v.lsplit_hi));
     if (split_parts(D.precision) == 2) TRY(dalloc_n(s, lsplit_bytes(n_alloc, D.precision), &v.lsplit_lo));

@@ -178,6 +178,7 @@ struct bo_space {
   int replay_steps = 0;
   int poisoned = BO_OK;
   bool coop_update = true;           // one cooperative launch per observation update
+  bool fused_acquire = false;        // tensor-core pass with the acquisition as its tail (one launch)
 };
 
 namespace bo {

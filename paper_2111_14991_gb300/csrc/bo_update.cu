@@ -5,10 +5,12 @@
 // Cholesky factor grows by one row and so does its inverse:
 //   K_new = [[K, k], [k^T, k(0) + jitter]],  l = L^-1 k,  d = sqrt(k(0) + jitter - l.l)
 //   L_new^-1 = [[L^-1, 0], [-(L^-T l)^T / d, 1 / d]].
-// Rows of L^-1 never change once written.  beta = L^-1 y~ is recomputed in
-// full because the standardization of y shifts with every observation.
-// The reduced-precision contraction gets a per-row scaled, split copy of each
-// new row (written once), see lsplit_offset().
+// Rows of L^-1 never change once written.  beta = L^-1 y~ and alpha = K^-1 y~
+// change in every entry when the standardization of y shifts, but both are
+// affine in its mean, so they follow from four vectors updated in O(n) per
+// observation (see the finish phase).  The reduced-precision contraction gets
+// a per-row scaled, split copy of each new row (written once), see
+// lsplit_offset().
 #include <algorithm>
 
 #include <cuda_fp16.h>
@@ -54,35 +56,68 @@ size_t lsplit_bytes(int n_max, int precision) {
 }
 
 // --- K3a: X[n] = x(idx), y[n] = y, visited bit, k_j = k(|x - X_j|) --------------
-__device__ __forceinline__ void obs_k_body(const DevView& v, int n, long long idx, double y_raw, int block) {
-  const int j = block * blockDim.x + threadIdx.x;
-  const double c = sqrt(2.0 * v.nu) / v.lengthscale;
-  if (block == 0 && threadIdx.x < v.d) {
+// (obs_record: the bookkeeping, by one block; obs_kj: one entry of k)
+__device__ __forceinline__ void obs_record(const DevView& v, int n, long long idx, double y_raw) {
+  if (threadIdx.x < v.d) {
+    const double c = sqrt(2.0 * v.nu) / v.lengthscale;
     const double x = coord64(v, idx, threadIdx.x);
     v.X[(size_t)n * v.d + threadIdx.x] = x;
     v.Xc[(size_t)n * v.d + threadIdx.x] = v.codes[(int64_t)threadIdx.x * v.N_pad + idx];
     if (v.xq) v.xq[xq_index(v.ds, n, threadIdx.x)] = (float)(x * (1.4426950408889634 * c));
   }
-  if (block == 0 && threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
     v.y[n] = y_raw;
     atomicOr(&v.visited[idx >> 5], 1u << (idx & 31));
   }
-  if (j < n) {
-    double r2 = 0.0;
-    if (v.sqd) {   // the prediction pass's arithmetic: a sum of tabulated squared differences
-      for (int p = 0; p < v.d; ++p) {
-        const int m = v.sqd_meta[v.d + 1 + p];
-        const int a = v.codes[(int64_t)p * v.N_pad + idx], b = v.Xc[(size_t)j * v.d + p];
-        r2 += v.sqd[v.sqd_meta[p] + a * m + b];
-      }
-    } else {
-      for (int p = 0; p < v.d; ++p) {
-        const double diff = coord64(v, idx, p) - v.X[(size_t)j * v.d + p];
+}
+
+// The new point's codes and coordinates and the table offsets, staged in
+// shared memory once per block, so that an entry of k needs one round of
+// loads (its observation's codes or coordinates, then the table entries)
+// instead of a chain of dependent global loads per parameter.
+struct KStage {
+  int off[BO_MAX_PARAMS];      // table offset of parameter p (tabulated distances)
+  int m[BO_MAX_PARAMS];        // value count of parameter p
+  int a[BO_MAX_PARAMS];        // the new point's value index of parameter p
+  double x[BO_MAX_PARAMS];     // the new point's coordinate of parameter p
+};
+
+__device__ __forceinline__ void k_stage(const DevView& v, long long idx, KStage& ks) {
+  for (int p = threadIdx.x; p < v.d; p += blockDim.x) {
+    ks.a[p] = v.codes[(int64_t)p * v.N_pad + idx];
+    ks.x[p] = v.vtab64[p * 256 + ks.a[p]];
+    if (v.sqd) {
+      ks.off[p] = v.sqd_meta[p];
+      ks.m[p] = v.sqd_meta[v.d + 1 + p];
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void obs_kj(const DevView& v, const KStage& ks, int j) {
+  const double c = sqrt(2.0 * v.nu) / v.lengthscale;
+  double r2 = 0.0;
+  if (v.sqd) {   // the prediction pass's arithmetic: a sum of tabulated squared differences
+#pragma unroll
+    for (int p = 0; p < BO_MAX_PARAMS; ++p)
+      if (p < v.d) r2 += v.sqd[ks.off[p] + ks.a[p] * ks.m[p] + v.Xc[(size_t)j * v.d + p]];
+  } else {
+#pragma unroll
+    for (int p = 0; p < BO_MAX_PARAMS; ++p)
+      if (p < v.d) {
+        const double diff = ks.x[p] - v.X[(size_t)j * v.d + p];
         r2 = fma(diff, diff, r2);
       }
-    }
-    v.kvec[j] = matern64(sqrt(r2), v.nu, c);
   }
+  v.kvec[j] = matern64(sqrt(r2), v.nu, c);
+}
+
+__device__ __forceinline__ void obs_k_body(const DevView& v, int n, long long idx, double y_raw, int block) {
+  __shared__ KStage ks;
+  const int j = block * blockDim.x + threadIdx.x;
+  if (block == 0) obs_record(v, n, idx, y_raw);
+  k_stage(v, idx, ks);
+  if (j < n) obs_kj(v, ks, j);
 }
 
 __global__ void obs_k_kernel(DevView v, int n, long long idx, double y_raw) {
@@ -142,63 +177,115 @@ __device__ __forceinline__ void obs_w_body(const DevView& v, int n, int bx, int 
 
 __global__ void obs_w_kernel(DevView v, int n) { obs_w_body(v, n, blockIdx.x, blockIdx.y); }
 
-// --- K3d: pivot, new row n of L^-1 and its split copy (one block) --------------
-__device__ __forceinline__ void obs_finish_body(const DevView& v, int n) {
-  __shared__ double red[32];
-  __shared__ double s_dinv;
+// --- K3d: pivot, new row n of L^-1 and its split copy, beta and alpha (one block)
+// beta = L^-1 y~ and alpha = K^-1 y~ = L^-T beta change in every entry when the
+// standardization y~ = (y - m) / std shifts, but both are affine in m:
+//   beta  = (u - (m - y0) e) / std,   u = L^-1 (y - y0),  e = L^-1 1
+//   alpha = (a - (m - y0) b) / std,   a = K^-1 (y - y0),  b = K^-1 1
+// (y0 = the first fitted value, a fixed shift that keeps u and a small).  u and
+// e grow by one entry per observation (rows of L^-1 never change): u_n =
+// row_n . (y - y0), e_n = row_n . 1.  a and b follow the bordered inverse
+//   K_new^-1 = [[K^-1 + w w^T / s, -w / s], [-w^T / s, 1 / s]],  w = K^-1 k,
+//   s = k(0) + jitter - l.l:  a_new = [a - w g, g],  g = ((y_n - y0) - k.a) / s
+// (the same for b with 1 - k.b), so the whole update of beta and alpha is O(n).
+
+// The pivot and every scalar of the new row follow from five sums over the
+// previous rows, formed in one block reduction (FP64 latency is long on this
+// GPU: one reduction and one pass over the row keep the serial chain short):
+//   l.l,  w.(y - y0),  w.1,  k.a,  k.b   and   max |w|   (w = L^-T l)
+// d^2 = k(0) + jitter - l.l;  the new row is [-w / d, 1 / d], so
+//   u_n = row . (y - y0) = ((y_n - y0) - w.(y - y0)) / d,  e_n = (1 - w.1) / d,
+//   g_a = ((y_n - y0) - k.a) / d^2,  g_b = (1 - k.b) / d^2,
+// and the row's largest magnitude, for the split copy's scale, is max|w| / d or 1 / d.
+__device__ __forceinline__ void obs_finish_body(const DevView& v, int n, double y_mean, double inv_std) {
+  __shared__ double red[6][32];
+  __shared__ double s_sc[8];   // dinv, d2, u_n, e_n, g_a, g_b, amax
   __shared__ float s_scale;
-  const int tid = threadIdx.x;
-  double ll = 0.0;
-  for (int i = tid; i < n; i += blockDim.x) ll = fma(v.lvec[i], v.lvec[i], ll);
-  ll = warp_sum(ll);
-  if ((tid & 31) == 0) red[tid >> 5] = ll;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    const double d2 = 1.0 + v.jitter - t;
-    s_dinv = (d2 > 0.0 && isfinite(d2)) ? 1.0 / sqrt(d2) : 0.0;
-    if (s_dinv == 0.0) v.stats->status = BO_ERR_NUMERIC;
-  }
-  __syncthreads();
-  const double dinv = s_dinv;
-  if (dinv == 0.0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+  const bool tc = v.precision != BO_PREC_FP64;
   const int nseg = (n + 63) / 64;
-  double* row = v.linv + (size_t)n * v.n_max;
-  double amax = 0.0;
-  for (int j = tid; j <= n; j += blockDim.x) {
-    double val;
-    if (j < n) {
-      double w = 0.0;
+  const double y0 = v.y[0];
+  auto w_of = [&](int j) {
+    double w = 0.0;
 #pragma unroll
-      for (int s = 0; s < 8; ++s)
-        if (s < nseg) w += v.wvec[(size_t)s * v.n_max + j];
-      val = -w * dinv;
-    } else {
-      val = dinv;
+    for (int s = 0; s < 8; ++s)
+      if (s < nseg) w += v.wvec[(size_t)s * v.n_max + j];
+    return w;
+  };
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // l.l, w.(y-y0), w.1, k.a, k.b, max|w|
+  for (int j = tid; j < n; j += blockDim.x) {
+    const double l = v.lvec[j], w = w_of(j);
+    acc[0] = fma(l, l, acc[0]);
+    acc[1] = fma(w, v.y[j] - y0, acc[1]);
+    acc[2] += w;
+    if (tc) {
+      acc[3] = fma(v.kvec[j], v.avec[j], acc[3]);
+      acc[4] = fma(v.kvec[j], v.bvec[j], acc[4]);
     }
-    row[j] = val;
-    amax = fmax(amax, fabs(val));
+    acc[5] = fmax(acc[5], fabs(w));
   }
-  if (v.precision == BO_PREC_FP64) return;
-  // per-row power-of-two scale s with max |row| * s in [2^13, 2^14)
-  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  __syncthreads();
-  if ((tid & 31) == 0) red[tid >> 5] = amax;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const double x = __shfl_xor_sync(0xffffffffu, acc[q], o);
+      acc[q] = q == 5 ? fmax(acc[q], x) : acc[q] + x;
+    }
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) red[q][warp] = acc[q];
   __syncthreads();
   if (tid == 0) {
-    double m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    int e;
-    frexp(m, &e);                       // m in [2^(e-1), 2^e)
-    s_scale = ldexpf(1.0f, 14 - e);
-    if (v.xq) v.xq[xq_index(v.ds, n, v.ds)] = 1.0f / (s_scale * s_scale);
+    double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < nw; ++w) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) t[q] += red[q][w];
+      t[5] = fmax(t[5], red[5][w]);
+    }
+    const double d2 = 1.0 + v.jitter - t[0];
+    const double dinv = (d2 > 0.0 && isfinite(d2)) ? 1.0 / sqrt(d2) : 0.0;
+    if (dinv == 0.0) v.stats->status = BO_ERR_NUMERIC;
+    const double dinv2 = dinv * dinv;
+    const double yn = v.y[n] - y0;
+    s_sc[0] = dinv;
+    s_sc[1] = d2;
+    s_sc[2] = (yn - t[1]) * dinv;
+    s_sc[3] = (1.0 - t[2]) * dinv;
+    s_sc[4] = (yn - t[3]) * dinv2;
+    s_sc[5] = (1.0 - t[4]) * dinv2;
+    s_sc[6] = fmax(t[5], 1.0) * dinv;
+    if (tc) {
+      // per-row power-of-two scale s with max |row| * s in [2^13, 2^14)
+      int e;
+      frexp(s_sc[6], &e);                 // amax in [2^(e-1), 2^e)
+      s_scale = ldexpf(1.0f, 14 - e);
+      v.xq[xq_index(v.ds, n, v.ds)] = 1.0f / (s_scale * s_scale);
+    }
+    v.uvec[n] = s_sc[2];
+    v.evec[n] = s_sc[3];
   }
   __syncthreads();
-  const float sc = s_scale;
+  const double dinv = s_sc[0];
+  if (dinv == 0.0) return;
+  const double pu = s_sc[2], pe = s_sc[3], ga = s_sc[4], gb = s_sc[5];
+  const double shift = y_mean - y0;
+  const float sc = tc ? s_scale : 0.0f;
   const int eb = split_elem_bytes(v.precision);
+  double* row = v.linv + (size_t)n * v.n_max;
   for (int j = tid; j <= n; j += blockDim.x) {
-    const float x = (float)row[j] * sc;
+    const double w = j < n ? w_of(j) : 0.0;
+    const double val = j < n ? -w * dinv : dinv;
+    row[j] = val;
+    const double u = j < n ? v.uvec[j] : pu, e = j < n ? v.evec[j] : pe;
+    v.beta[j] = (u - shift * e) * inv_std;
+    if (!tc) continue;
+    const double a = j < n ? fma(-w, ga, v.avec[j]) : ga;
+    const double b = j < n ? fma(-w, gb, v.bvec[j]) : gb;
+    v.avec[j] = a;
+    v.bvec[j] = b;
+    v.xq[xq_index(v.ds, j, v.ds + 1)] = (float)((a - shift * b) * inv_std);
+    // the split copy of row n, element j
+    const float x = (float)val * sc;
     const size_t off = lsplit_offset(v.n_max, eb, n, j);
     if (v.precision == BO_PREC_FP16X3) {
       const __half h = __float2half_rn(x);
@@ -211,55 +298,21 @@ __device__ __forceinline__ void obs_finish_body(const DevView& v, int n) {
       *reinterpret_cast<__nv_bfloat16*>(v.lsplit_hi + off) = h;
       *reinterpret_cast<__nv_bfloat16*>(v.lsplit_lo + off) = l;
     } else {  // TF32: round to nearest (ties away) to 10 explicit mantissa bits
-      uint32_t u;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
-      *reinterpret_cast<uint32_t*>(v.lsplit_hi + off) = u;
+      uint32_t hu;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hu) : "f"(x));
+      *reinterpret_cast<uint32_t*>(v.lsplit_hi + off) = hu;
       if (v.precision == BO_PREC_TF32X3) {   // lo = the rounding residual, itself rounded to TF32
-        uint32_t w;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w) : "f"(x - __uint_as_float(u)));
-        *reinterpret_cast<uint32_t*>(v.lsplit_lo + off) = w;
+        uint32_t lu;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lu) : "f"(x - __uint_as_float(hu)));
+        *reinterpret_cast<uint32_t*>(v.lsplit_lo + off) = lu;
       }
     }
   }
 }
 
-__global__ void obs_finish_kernel(DevView v, int n) { obs_finish_body(v, n); }
-
-
-// --- K3e: beta = L^-1 y~ for rows 0..n ------------------------------------------
-__device__ __forceinline__ void obs_beta_body(const DevView& v, int rows, double y_mean, double inv_std,
-                                              int block) {
-  const int warp = (block * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= rows) return;
-  const double* row = v.linv + (size_t)warp * v.n_max;
-  double s = 0.0;
-  for (int j = lane; j <= warp; j += 32) s = fma(row[j], (v.y[j] - y_mean) * inv_std, s);
-  s = warp_sum(s);
-  if (lane == 0) v.beta[warp] = s;
+__global__ void obs_finish_kernel(DevView v, int n, double y_mean, double inv_std) {
+  obs_finish_body(v, n, y_mean, inv_std);
 }
-
-// --- K3f (tensor-core forms): alpha = L^-T beta, so that mu = k* . alpha -------
-// (warp per column j: lanes stride down the rows i >= j of L^-1, fixed-order
-// reduction).  The prediction pass evaluates mu from K* and alpha directly:
-// the FP32 error of mu is then bounded by sum_j |alpha_j k*_j| times the K*
-// and accumulation rounding, and does not depend on the split contraction.
-__device__ __forceinline__ void obs_alpha_body(const DevView& v, int rows, int block) {
-  if (v.precision == BO_PREC_FP64) return;
-  const int col = (block * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (col >= rows) return;
-  double s = 0.0;
-  for (int i = col + lane; i < rows; i += 32) s = fma(v.linv[(size_t)i * v.n_max + col], v.beta[i], s);
-  s = warp_sum(s);
-  if (lane == 0) v.xq[xq_index(v.ds, col, v.ds + 1)] = (float)s;
-}
-
-__global__ void obs_beta_kernel(DevView v, int rows, double y_mean, double inv_std) {
-  obs_beta_body(v, rows, y_mean, inv_std, blockIdx.x);
-}
-
-__global__ void obs_alpha_kernel(DevView v, int rows) { obs_alpha_body(v, rows, blockIdx.x); }
 
 // ---- the same phases over many spaces: block b serves item blocks[b].item ----
 __global__ void obs_k_batch(const ObsItem* items, const ObsBlock* blocks) {
@@ -283,19 +336,7 @@ __global__ void obs_w_batch(const ObsItem* items, const ObsBlock* blocks) {
 
 __global__ void obs_finish_batch(const ObsItem* items) {
   const ObsItem& it = items[blockIdx.x];
-  obs_finish_body(it.v, it.n);
-}
-
-__global__ void obs_beta_batch(const ObsItem* items, const ObsBlock* blocks) {
-  const ObsBlock b = blocks[blockIdx.x];
-  const ObsItem& it = items[b.item];
-  obs_beta_body(it.v, it.n + 1, it.y_mean, it.inv_std, b.local);
-}
-
-__global__ void obs_alpha_batch(const ObsItem* items, const ObsBlock* blocks) {
-  const ObsBlock b = blocks[blockIdx.x];
-  const ObsItem& it = items[b.item];
-  obs_alpha_body(it.v, it.n + 1, b.local);
+  obs_finish_body(it.v, it.n, it.y_mean, it.inv_std);
 }
 
 __global__ void set_visited_batch(const VisitItem* items, int count) {
@@ -319,8 +360,7 @@ void obs_batch_blocks(const int* n, int count, std::vector<ObsBlock>* blocks, in
   add([](int m) { return (m + 31) / 32 + (m == 0); }, 0);             // k: 32 threads
   add([](int m) { return (m + 7) / 8; }, 1);                          // l: warp per row
   add([](int m) { return ((m + 31) / 32) * ((m + 63) / 64); }, 2);    // w: 32 columns x 64 rows
-  add([](int m) { return (m + 1 + 7) / 8; }, 3);                      // beta: warp per row
-  add([](int m) { return (m + 1 + 7) / 8; }, 4);                      // alpha: warp per column
+  counts[3] = counts[4] = 0;                                          // beta, alpha: in the finish
 }
 
 int launch_observe_batch(const ObsItem* items, int count, const ObsBlock* blocks, const int counts[5],
@@ -336,10 +376,8 @@ int launch_observe_batch(const ObsItem* items, int count, const ObsBlock* blocks
     b += counts[2];
     obs_finish_batch<<<count, 512, 0, s>>>(items);
     ++launches;
-    if (counts[3]) { obs_beta_batch<<<counts[3], 256, 0, s>>>(items, b); ++launches; }
-    b += counts[3];
-    if (counts[4] && tc) { obs_alpha_batch<<<counts[4], 256, 0, s>>>(items, b); ++launches; }
   }
+  (void)tc;
   if (n_visits > 0) {
     set_visited_batch<<<(n_visits + 127) / 128, 128, 0, s>>>(visits, n_visits);
     ++launches;
@@ -353,10 +391,11 @@ int launch_set_visited(const DevView& v, int64_t idx, cudaStream_t s) {
 }
 
 // ---- the whole update of one space in one cooperative launch ----------------
-// The phases above run as virtual blocks of 256 threads over a co-resident
-// grid, separated by grid barriers (arrival counter in DevStats, bounded wait:
-// on expiry the update records BO_ERR_TIMEOUT and every block leaves).  One
-// launch instead of six saves the launch gaps that dominate at small n.
+// The phases above (k, l, w, finish) run as virtual blocks of 256 threads over
+// a co-resident grid, separated by three grid barriers (arrival counter in
+// DevStats, bounded wait: on expiry the update records BO_ERR_TIMEOUT and
+// every block leaves).  One launch instead of four saves the launch gaps that
+// dominate at small n.
 constexpr int kFusedThreads = 256;
 constexpr unsigned long long kCoopWaitNs = 2000000000ull;
 
@@ -393,11 +432,15 @@ __global__ void __launch_bounds__(kFusedThreads) obs_fused_kernel(DevView v, int
                                                                   double y_mean, double inv_std) {
   DevStats* st = v.stats;
   const int G = (int)gridDim.x;
-  const int rows = n + 1;
   unsigned int phase = 0;
   do {
-    for (int b = blockIdx.x; b < (n + kFusedThreads - 1) / kFusedThreads + (n == 0); b += G)
-      obs_k_body(v, n, idx, y_raw, b);
+    // k over all blocks (entry j on block j mod G): its FP64 Matern chains run side by side
+    if (blockIdx.x == 0) obs_record(v, n, idx, y_raw);
+    {
+      __shared__ KStage ks;
+      k_stage(v, idx, ks);
+      for (int j = blockIdx.x + G * threadIdx.x; j < n; j += G * kFusedThreads) obs_kj(v, ks, j);
+    }
     if (n > 0) {
       if (!coop_sync(st, ++phase)) break;
       for (int b = blockIdx.x; b < (n + 7) / 8; b += G) obs_l_body(v, n, b);
@@ -409,13 +452,7 @@ __global__ void __launch_bounds__(kFusedThreads) obs_fused_kernel(DevView v, int
       }
     }
     if (!coop_sync(st, ++phase)) break;
-    if (blockIdx.x == 0) obs_finish_body(v, n);
-    if (!coop_sync(st, ++phase)) break;
-    for (int b = blockIdx.x; b < (rows + 7) / 8; b += G) obs_beta_body(v, rows, y_mean, inv_std, b);
-    if (v.precision != BO_PREC_FP64) {
-      if (!coop_sync(st, ++phase)) break;
-      for (int b = blockIdx.x; b < (rows + 7) / 8; b += G) obs_alpha_body(v, rows, b);
-    }
+    if (blockIdx.x == 0) obs_finish_body(v, n, y_mean, inv_std);
   } while (false);
   // the last block to leave resets the barrier state for the next update
   __syncthreads();
@@ -465,11 +502,9 @@ int fused_update_grid(int n) {
     }
     max_blocks = co_resident[dev];
   }
-  const int rows = n + 1;
   int want = std::max(1, (n + kFusedThreads - 1) / kFusedThreads);
   want = std::max(want, (n + 7) / 8);
   want = std::max(want, ((n + 31) / 32) * ((n + 63) / 64));
-  want = std::max(want, (rows + 7) / 8);
   return std::min(want, max_blocks);
 }
 
@@ -498,14 +533,8 @@ int launch_observe_update(bool cooperative, const DevView& v, int n, int64_t idx
     obs_w_kernel<<<gw, 256, 0, s>>>(v, n);
     launches += 2;
   }
-  obs_finish_kernel<<<1, 512, 0, s>>>(v, n);
-  const int rows = n + 1;
-  obs_beta_kernel<<<(rows + 7) / 8, 256, 0, s>>>(v, rows, y_mean, 1.0 / y_std);
-  launches += 2;
-  if (v.precision != BO_PREC_FP64) {
-    obs_alpha_kernel<<<(rows + 7) / 8, 256, 0, s>>>(v, rows);
-    ++launches;
-  }
+  obs_finish_kernel<<<1, 512, 0, s>>>(v, n, y_mean, 1.0 / y_std);
+  ++launches;
   return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 

@@ -1,8 +1,8 @@
 """The two forms of the single-space observation update agree.
 
-By default a space's FP64 update (k, l = L^-1 k, w, pivot row, beta, alpha)
-runs as one cooperative launch; with BO_NO_COOP set at creation it runs as six
-phase launches.  Both must give the same factor and posterior: the only
+By default a space's FP64 update (k, l = L^-1 k, w, then the pivot row with
+beta and alpha) runs as one cooperative launch; with BO_NO_COOP set at
+creation it runs as four phase launches.  Both must give the same factor and posterior: the only
 difference is the block width of the pivot's reduction, whose last-bit
 difference the conditioning of K (about 1e7 here) can amplify; so the results
 must agree to 1e-9 of their scale (the FP64 parity bar is 1e-6) in FP64 mode,
@@ -58,3 +58,46 @@ def test_cooperative_and_phase_updates_agree(precision):
     tol = 1e-9 if precision == "fp64" else 1e-5
     assert np.max(np.abs(a[2] - b[2])) <= tol and np.max(np.abs(a[3] - b[3])) <= tol, precision
     assert a[4] < b[4]                              # one launch per update instead of several
+
+
+def suggest_run(sp, land, precision, fused, steps=25, seed=3):
+    """EI suggestions with the given observations fed in order; with fused
+    (BO_FUSED_ACQ) the tensor-core pass carries the acquisition as its tail
+    (one cooperative launch), without it the acquisition is its own launch."""
+    from paper_2111_14991_gb300 import Space
+    old = os.environ.pop("BO_FUSED_ACQ", None)
+    if fused:
+        os.environ["BO_FUSED_ACQ"] = "1"
+    try:
+        s = Space(sp.grids, sp.invalid, precision=precision, n_max=128)
+    finally:
+        os.environ.pop("BO_FUSED_ACQ", None)
+        if old is not None:
+            os.environ["BO_FUSED_ACQ"] = old
+    for i in W.random_initial_sample(sp.n_valid, 20, seed):
+        s.observe(int(i), float(land.clean([i])[0]))
+    out = []
+    for _ in range(steps):
+        r = s.suggest()
+        out.append(r)
+        s.observe(r["idx"], float(land.clean([r["idx"]])[0]))
+    launches = s.launch_count()
+    s.close()
+    return out, launches
+
+
+@pytest.mark.parametrize("precision", ["fp16x3", "tf32x3"])
+def test_fused_and_separate_acquisition_agree(precision):
+    """The acquisition tail of the prediction pass and the separate acquisition
+    kernel score with the same FP32 arithmetic and keep the same (score, index)
+    order: the same suggestions, scores, lambda and mean variance."""
+    sp = W.paper_shaped_space("pnpoly")
+    land = W.Landscape(sp, 9)
+    a, la = suggest_run(sp, land, precision, fused=True)
+    b, lb = suggest_run(sp, land, precision, fused=False)
+    for t, (x, z) in enumerate(zip(a, b)):
+        assert x["idx"] == z["idx"], (t, x, z)
+        assert x["score"] == z["score"] and x["mu"] == z["mu"] and x["sigma"] == z["sigma"], (t, x, z)
+        assert x["lam"] == pytest.approx(z["lam"], rel=1e-12)
+        assert x["mean_var"] == pytest.approx(z["mean_var"], rel=1e-12)
+    assert la < lb                                  # one launch per pass instead of two
