@@ -63,13 +63,17 @@ MEETS_BAR = ("fp16x3", "tf32x3")
 # dram bytes per launch of the dominant kernel from an ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (null once the source changes)
 TRAFFIC = {
-    "predict_f64": [{"bytes_per_launch": 1117440 + 0, "src_sha": "7db7286ecbec0617", "n": 220, "N": 113247,
+    "predict_f64": [{"bytes_per_launch": 1117952 + 0, "src_sha": "1e61086996b2c63c", "n": 220, "N": 113247,
                      "capture": "profiles/predict_f64_gemm7p_n220.md"}],
     "predict_tc_fp16x3": [
-        {"bytes_per_launch": 10716672 + 3584, "src_sha": "881cb10161712188", "n": 512, "N": 1032469,
+        {"bytes_per_launch": 10716928 + 4096, "src_sha": "62774086942f8921", "n": 512, "N": 1032469,
          "capture": "profiles/predict_tc_fp16x3_gemm9p_n512.md"},
-        {"bytes_per_launch": 1005568 + 0, "src_sha": "881cb10161712188", "n": 220, "N": 113247,
+        {"bytes_per_launch": 1001728 + 256, "src_sha": "62774086942f8921", "n": 220, "N": 113247,
          "capture": "profiles/predict_tc_fp16x3_gemm7p_n220.md"},
+    ],
+    "predict_tc_tf32x3": [
+        {"bytes_per_launch": 11237888 + 3328, "src_sha": "62774086942f8921", "n": 512, "N": 1032469,
+         "capture": "profiles/predict_tc_tf32x3_gemm9p_n512.md"},
     ],
 }
 
