@@ -28,7 +28,9 @@
  *     a space's observation update runs as four phase launches instead of one
  *     cooperative launch), BO_FUSED_ACQ (set: a reduced-precision space's
  *     prediction pass carries the acquisition as its tail, one cooperative
- *     launch instead of two; the same results) and BO_NO_GRAPH (set: a batch
+ *     launch instead of two; the same results), BO_NO_PDL (read once per
+ *     process; set: the kernels of a pass are launched without programmatic
+ *     dependent launch; the same results) and BO_NO_GRAPH (set: a batch
  *     launches its kernels one by one instead of replaying a captured CUDA
  *     graph).  Results are the same up to the reduction order of the
  *     update's pivot.

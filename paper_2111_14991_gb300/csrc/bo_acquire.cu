@@ -9,6 +9,7 @@
 // across the warp with shuffles, across the block in shared memory, and
 // across blocks by the last block to finish.  Ties go to the lower index.
 #include <cfloat>
+#include <cstdlib>
 #include <climits>
 
 #include "bo_acquire_dev.cuh"
@@ -297,6 +298,7 @@ __device__ __forceinline__ void acquire_body(const AcqDev& v, const PassArgs& a,
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a) {
+  pdl_wait();                 // the prediction pass has completed (dependent launch)
   if constexpr (sizeof(T) == 4)
     acquire_body_f32(v, a, blockIdx.x, gridDim.x, *v.sum_var);
   else
@@ -327,6 +329,11 @@ __global__ void __launch_bounds__(kThreads) acquire_batch_kernel(const AcqItem* 
 
 }  // namespace
 
+bool pdl_enabled() {
+  static const bool on = getenv("BO_NO_PDL") == nullptr;
+  return on;
+}
+
 int acquire_grid(int64_t n_cand, int max_blocks, int per_thread) {
   const int64_t want = (n_cand + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
   return (int)(want < max_blocks ? (want < 1 ? 1 : want) : max_blocks);
@@ -334,11 +341,9 @@ int acquire_grid(int64_t n_cand, int max_blocks, int per_thread) {
 
 int launch_acquire(const AcqDev& v, const PassArgs& a, bool f64, cudaStream_t s) {
   const int grid = acquire_grid(v.N, v.max_blocks, 2);
-  if (f64)
-    acquire_kernel<double><<<grid, kThreads, 0, s>>>(v, a);
-  else
-    acquire_kernel<float><<<grid, kThreads, 0, s>>>(v, a);
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  const cudaError_t e = f64 ? launch_ex(acquire_kernel<double>, dim3(grid), dim3(kThreads), 0, s, pdl_enabled(), v, a)
+                            : launch_ex(acquire_kernel<float>, dim3(grid), dim3(kThreads), 0, s, pdl_enabled(), v, a);
+  return e == cudaSuccess ? 1 : -1;
 }
 
 int launch_acquire_batch(const AcqItem* items, const int* block_item, const int* block_local,

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -120,7 +121,35 @@ inline bool ensure_dynamic_smem(const void* kernel, size_t (&configured)[kMaxDev
   return true;
 }
 
+// Programmatic dependent launch: kernels of one pass (update -> prediction ->
+// acquisition) may be launched as dependents of the previous kernel in the
+// stream, so that their launch and prologue overlap its tail.  A dependent
+// waits (pdl_wait) for the predecessor to complete, its memory visible,
+// before it reads or writes anything the predecessor touches; a kernel
+// launched without the attribute passes pdl_wait at once.  With BO_NO_PDL set
+// in the environment (read once per process) they are launched plainly.
+bool pdl_enabled();
+// Launch `kernel` on s with the programmatic-serialization attribute when pdl.
+template <typename... Params, typename... Args>
+cudaError_t launch_ex(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                      Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 #ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Sum of count per-block partials (written by other blocks, made visible by
 // the caller's fence / counter protocol), by every thread of a block: each
 // thread adds its strided share in order, a fixed warp butterfly and a

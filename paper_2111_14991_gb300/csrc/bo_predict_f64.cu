@@ -71,6 +71,7 @@ __device__ __forceinline__ void slice_groups(int q_lo, int q_hi, const double* K
 // and squares on the narrow FP64 pipe.
 template <int BM, bool TAB>
 __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int n, int n_pad) {
+  pdl_wait();                             // the observation update has completed (dependent launch)
   constexpr int TM = BM / 16;             // rows per thread
   extern __shared__ double smem[];
   const int d = v.d;
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
       if (i < v.N && !((v.visited[i >> 5] >> (i & 31)) & 1u)) vsum += var;
     }
   }
+  pdl_trigger();                           // the acquisition may be launched (it waits for completion)
   // block sum of variances in a fixed order
   for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
   if ((tid & 31) == 0) red[tid >> 5] = vsum;
@@ -238,8 +240,10 @@ int launch_bm(const DevView& v, int n, cudaStream_t s) {
   if (!ensure_dynamic_smem((const void*)predict_f64_kernel<BM, TAB>, configured, sm)) return -1;
   const int grid = (int)(v.N_pad / BM);
   if (grid > v.max_partials) return -1;
-  predict_f64_kernel<BM, TAB><<<grid, kThreads, sm, s>>>(v, n, n_pad);
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  return launch_ex(predict_f64_kernel<BM, TAB>, dim3(grid), dim3(kThreads), sm, s, pdl_enabled(), v, n, n_pad) ==
+                 cudaSuccess
+             ? 1
+             : -1;
 }
 
 }  // namespace

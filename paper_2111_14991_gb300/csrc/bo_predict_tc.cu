@@ -613,6 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  pdl_wait();              // the observation update has completed (dependent launch); setup overlapped it
   const uint32_t tmem = *tmem_slot;
   const uint32_t xs_base = smem_addr(smem + P.off_x);
   double vsum = 0.0;
@@ -1097,6 +1098,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
   }
 
   // ---- teardown: TMEM release; one space: per-CTA variance sum, last-block total
+  pdl_trigger();           // the acquisition may be launched (it waits for completion)
   for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
   if (warp >= kEpiWarp0 && warp < kMmaWarp && lane == 0) red[warp - kEpiWarp0] = vsum;
   tc_fence_before();
@@ -1150,6 +1152,11 @@ template <int MODE, int DMAX, bool NU52>
 int launch_mode(const TcParams& P, size_t smem, int grid, bool coop, cudaStream_t s) {
   static size_t configured[kMaxDevices] = {};
   if (!ensure_dynamic_smem((const void*)predict_tc_kernel<MODE, DMAX, NU52>, configured, smem)) return -1;
+  if (!coop && P.batch == 0)   // one space: a dependent launch after its observation update
+    return launch_ex(predict_tc_kernel<MODE, DMAX, NU52>, dim3(grid), dim3(kThreads), smem, s, pdl_enabled(), P) ==
+                   cudaSuccess
+               ? 1
+               : -1;
   if (coop) {
     void* args[] = {const_cast<TcParams*>(&P)};
     if (cudaLaunchCooperativeKernel((const void*)predict_tc_kernel<MODE, DMAX, NU52>, dim3(grid), dim3(kThreads),

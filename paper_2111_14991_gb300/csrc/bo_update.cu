@@ -430,6 +430,7 @@ __device__ __forceinline__ bool coop_sync(DevStats* st, unsigned int phase) {
 
 __global__ void __launch_bounds__(kFusedThreads) obs_fused_kernel(DevView v, int n, long long idx, double y_raw,
                                                                   double y_mean, double inv_std) {
+  pdl_trigger();           // the prediction pass may be launched now (it waits for this update)
   DevStats* st = v.stats;
   const int G = (int)gridDim.x;
   unsigned int phase = 0;
