@@ -47,7 +47,7 @@ def twins(precision):
     return alone, member, lands
 
 
-@pytest.mark.parametrize("precision", ["fp16x3", "tf32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp16x3", "tf32x3", "tf32", "fp64"])
 def test_batch_equals_alone(precision):
     from paper_2111_14991_gb300 import Batch
     alone, member, lands = twins(precision)
