@@ -63,16 +63,16 @@ MEETS_BAR = ("fp16x3", "tf32x3")
 # dram bytes per launch of the dominant kernel from an ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (null once the source changes)
 TRAFFIC = {
-    "predict_f64": [{"bytes_per_launch": 1117952 + 0, "src_sha": "1e61086996b2c63c", "n": 220, "N": 113247,
+    "predict_f64": [{"bytes_per_launch": 1119232 + 0, "src_sha": "72387f17a0fb2e5e", "n": 220, "N": 113247,
                      "capture": "profiles/predict_f64_gemm7p_n220.md"}],
     "predict_tc_fp16x3": [
-        {"bytes_per_launch": 10716928 + 4096, "src_sha": "62774086942f8921", "n": 512, "N": 1032469,
+        {"bytes_per_launch": 10720000 + 512, "src_sha": "f1d2a63e541b9ab6", "n": 512, "N": 1032469,
          "capture": "profiles/predict_tc_fp16x3_gemm9p_n512.md"},
-        {"bytes_per_launch": 1001728 + 256, "src_sha": "62774086942f8921", "n": 220, "N": 113247,
+        {"bytes_per_launch": 1001472 + 512, "src_sha": "f1d2a63e541b9ab6", "n": 220, "N": 113247,
          "capture": "profiles/predict_tc_fp16x3_gemm7p_n220.md"},
     ],
     "predict_tc_tf32x3": [
-        {"bytes_per_launch": 11237888 + 3328, "src_sha": "62774086942f8921", "n": 512, "N": 1032469,
+        {"bytes_per_launch": 11238656 + 3328, "src_sha": "f1d2a63e541b9ab6", "n": 512, "N": 1032469,
          "capture": "profiles/predict_tc_tf32x3_gemm9p_n512.md"},
     ],
 }
