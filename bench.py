@@ -60,6 +60,7 @@ PARITY = {
     (3, "tf32"): dict(mu=2.2e-4, sigma=4.5e-2, mu_strict=0.056, sigma_strict=1.0),
 }
 MEETS_BAR = ("fp16x3", "tf32x3")
+LAT_WARM = 50             # warm-up suggest calls before the latency sample
 # dram bytes per launch of the dominant kernel from an ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (null once the source changes)
 TRAFFIC = {
@@ -537,7 +538,7 @@ def measure_serving(count, rate, duration, precision, extra=160, seed=0, budget_
 
 def measure_latency(cfg_id, precision, reps, flush):
     """bo_suggest latency (host entry to index returned) at the final state of
-    a configuration, after 10 warm-up calls, L2 flushed before each call."""
+    a configuration, after LAT_WARM warm-up calls, L2 flushed before each call."""
     import torch
     from paper_2111_14991_gb300 import Space
     cfg = CONFIGS[cfg_id]
@@ -547,12 +548,12 @@ def measure_latency(cfg_id, precision, reps, flush):
     for i, v in zip(idx, y):
         s.observe(int(i), float(v))
     lat, scored = [], 0
-    for t in range(10 + reps):
+    for t in range(LAT_WARM + reps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         info = s.suggest()
-        if t >= 10:
+        if t >= LAT_WARM:
             lat.append(time.perf_counter() - t0)
             scored += info["n_scored"]
     s.close()
@@ -602,12 +603,12 @@ def run_ours(args, rank, world):
         e2e_scored += info["n_scored"]
     # suggest latency at the final state (single AF: every call is a full pass)
     lat = []
-    for t in range(10 + max(args.latency_reps, steps)):
+    for t in range(LAT_WARM + max(args.latency_reps, steps)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.suggest()
-        if t >= 10:
+        if t >= LAT_WARM:
             lat.append(time.perf_counter() - t0)
     s.close()
     e2e_tot = sum(e2e_t)
@@ -634,7 +635,7 @@ def run_ours(args, rank, world):
                                       note=None if fprec in MEETS_BAR else "does not meet 1e-3 on sigma",
                                       source="tests/test_gpu_tc.py::test_full_size, 10k-candidate subsample")
             forms[f"config{fcfg}/{fprec}"] = form
-        lat1 = measure_latency(1, "fp64", max(args.latency_reps, 100), flush)
+        lat1 = measure_latency(1, "fp64", args.latency_reps, flush)
         forms["config1/fp64-latency"] = dict(lat1, workload=CONFIGS[1]["name"])
         if not args.no_serving:
             forms["config5/fp16x3-served"] = measure_serving(args.serve_sessions, 2000.0, 4.0, "fp16x3")
@@ -839,7 +840,7 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=sorted(CONFIGS))
     ap.add_argument("--precision", default="fp64", choices=sorted(DTYPE))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--latency-reps", type=int, default=200)
+    ap.add_argument("--latency-reps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (256-session) form")
