@@ -216,6 +216,20 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       : "memory");
 }
 
+// L2 prefetch of this CTA's share (1 / parts) of [p, p + bytes): the shares of
+// all CTAs cover the range; 16-byte granules (the bulk prefetch's unit).
+__device__ __forceinline__ void l2_prefetch_share(const void* p, size_t bytes, int part, int parts) {
+  const size_t per = ((bytes + (size_t)parts - 1) / (size_t)parts + 15) & ~(size_t)15;
+  size_t lo = per * (size_t)part;
+  const size_t hi = min(bytes & ~(size_t)15, lo + per);
+  while (lo < hi) {
+    const uint32_t len = (uint32_t)min(hi - lo, (size_t)(1u << 20));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const uint8_t*>(p) + lo), "r"(len)
+                 : "memory");
+    lo += len;
+  }
+}
+
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -609,6 +623,17 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
                  "r"(P.tmem_cols * P.acc_stages) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // one space, launched as a dependent of its observation update: while the update runs, pull
+  // the inputs that the L2 flush between passes leaves in HBM (the split L^-1 copy, the
+  // candidate codes) into L2; a prefetch is a hint only, every read follows pdl_wait below
+  if (P.batch == 0 && warp == kLoadWarp && lane == 0) {
+    const TcSess& S = P.s0;
+    const size_t lbytes = (size_t)kChunkBytes * ((size_t)S.chunks * S.n_max -
+                                                  (size_t)P.cw * S.chunks * (S.chunks - 1) / 2);
+    l2_prefetch_share(S.lhi, lbytes, blockIdx.x, gridDim.x);
+    if (P.parts == 2) l2_prefetch_share(S.llo, lbytes, blockIdx.x, gridDim.x);
+    l2_prefetch_share(S.codes, (size_t)S.d * (size_t)S.N_pad, blockIdx.x, gridDim.x);
   }
   tc_fence_before();
   __syncthreads();
