@@ -428,9 +428,42 @@ __device__ __forceinline__ bool coop_sync(DevStats* st, unsigned int phase) {
   return *(volatile int32_t*)&st->coop_abort == 0;
 }
 
+// L2 prefetch of this block's share (1 / parts) of [p, p + bytes), in whole 16-byte granules
+// (a partial last granule is left out, so nothing past the range is touched).
+__device__ __forceinline__ void l2_prefetch_share(const void* p, size_t bytes, int part, int parts) {
+  if (!p) return;
+  const size_t per = ((bytes + (size_t)parts - 1) / (size_t)parts + 15) & ~(size_t)15;
+  size_t lo = per * (size_t)part;
+  const size_t hi = min(bytes & ~(size_t)15, lo + per);
+  while (lo < hi) {
+    const uint32_t len = (uint32_t)min(hi - lo, (size_t)(1u << 20));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const uint8_t*>(p) + lo), "r"(len)
+                 : "memory");
+    lo += len;
+  }
+}
+
 __global__ void __launch_bounds__(kFusedThreads) obs_fused_kernel(DevView v, int n, long long idx, double y_raw,
                                                                   double y_mean, double inv_std) {
   pdl_trigger();           // the prediction pass may be launched now (it waits for this update)
+  // the phases' inputs into L2 first (an L2 flush between passes leaves them in HBM): the rows of
+  // L^-1 (phases l, w), the observations' value indices / coordinates and tables (phase k), the
+  // vectors the pivot phase reads; prefetches are hints, the phases read after their barriers
+  if (threadIdx.x == 0) {
+    const int G = (int)gridDim.x, b = (int)blockIdx.x;
+    const size_t r8 = (size_t)n * 8;     // exact sizes: the prefetch stops at their last whole granule
+    l2_prefetch_share(v.linv, (size_t)n * v.n_max * 8, b, G);
+    if (b == G - 1) {
+      l2_prefetch_share(v.Xc, (size_t)n * v.d, 0, 1);
+      if (v.sqd) l2_prefetch_share(v.sqd, (size_t)v.sqd_total * 8, 0, 1);
+      else l2_prefetch_share(v.X, (size_t)n * v.d * 8, 0, 1);
+      l2_prefetch_share(v.y, r8, 0, 1);
+      l2_prefetch_share(v.uvec, r8, 0, 1);
+      l2_prefetch_share(v.evec, r8, 0, 1);
+      l2_prefetch_share(v.avec, r8, 0, 1);
+      l2_prefetch_share(v.bvec, r8, 0, 1);
+    }
+  }
   DevStats* st = v.stats;
   const int G = (int)gridDim.x;
   unsigned int phase = 0;
