@@ -101,3 +101,50 @@ def test_fused_and_separate_acquisition_agree(precision):
         assert x["lam"] == pytest.approx(z["lam"], rel=1e-12)
         assert x["mean_var"] == pytest.approx(z["mean_var"], rel=1e-12)
     assert la < lb                                  # one launch per pass instead of two
+
+
+PDL_CHILD = r"""
+import json, sys
+import numpy as np
+sys.path.insert(0, ".")
+from paper_2111_14991_gb300 import Space, build
+from paper_2111_14991_gb300 import workloads as W
+build.build()
+sp = W.paper_shaped_space("pnpoly")
+land = W.Landscape(sp, 11)
+out = {}
+for precision in ("fp16x3", "fp64"):
+    s = Space(sp.grids, sp.invalid, precision=precision, n_max=64)
+    for i in W.random_initial_sample(sp.n_valid, 20, 11):
+        s.observe(int(i), float(land.clean([i])[0]))
+    picks = []
+    for _ in range(10):
+        r = s.suggest()
+        picks.append([int(r["idx"]), float(r["score"]), float(r["lam"])])
+        s.observe(r["idx"], float(land.clean([r["idx"]])[0]))
+    mu, var = s.predict()
+    s.close()
+    out[precision] = dict(picks=picks, mu=float(np.sum(np.abs(mu))), var=float(np.sum(var)))
+print(json.dumps(out))
+"""
+
+
+def test_dependent_launches_change_nothing():
+    """Programmatic dependent launches (the default) and plain launches
+    (BO_NO_PDL, read once per process: each setting runs in its own process)
+    give the same suggestions, scores and posteriors, bit for bit."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = []
+    for pdl in (True, False):
+        env = dict(os.environ)
+        env.pop("BO_NO_PDL", None)
+        if not pdl:
+            env["BO_NO_PDL"] = "1"
+        r = subprocess.run([sys.executable, "-c", PDL_CHILD], cwd=root, env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        res.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    assert res[0] == res[1]
