@@ -67,13 +67,13 @@ TRAFFIC = {
     "predict_f64": [{"bytes_per_launch": 1119232 + 0, "src_sha": "72387f17a0fb2e5e", "n": 220, "N": 113247,
                      "capture": "profiles/predict_f64_gemm7p_n220.md"}],
     "predict_tc_fp16x3": [
-        {"bytes_per_launch": 10720000 + 512, "src_sha": "f1d2a63e541b9ab6", "n": 512, "N": 1032469,
+        {"bytes_per_launch": 10720768 + 2048, "src_sha": "2b082af929346ace", "n": 512, "N": 1032469,
          "capture": "profiles/predict_tc_fp16x3_gemm9p_n512.md"},
-        {"bytes_per_launch": 1001472 + 512, "src_sha": "f1d2a63e541b9ab6", "n": 220, "N": 113247,
+        {"bytes_per_launch": 1005824 + 512, "src_sha": "2b082af929346ace", "n": 220, "N": 113247,
          "capture": "profiles/predict_tc_fp16x3_gemm7p_n220.md"},
     ],
     "predict_tc_tf32x3": [
-        {"bytes_per_launch": 11238656 + 3328, "src_sha": "f1d2a63e541b9ab6", "n": 512, "N": 1032469,
+        {"bytes_per_launch": 11241728 + 3840, "src_sha": "2b082af929346ace", "n": 512, "N": 1032469,
          "capture": "profiles/predict_tc_tf32x3_gemm9p_n512.md"},
     ],
 }
