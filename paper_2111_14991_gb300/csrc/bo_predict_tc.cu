@@ -209,6 +209,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   return true;
 }
 
+// mbar_wait by every lane of a warp; the result is the same in all lanes
+// (false if any lane's wait expired or saw the abort flag).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int32_t* status) {
+  return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_flag, status));
+}
+
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -293,6 +300,31 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_addr(bar))
                : "memory");
+}
+
+// The MMA-issuing warps run their loops with all 32 lanes, so that the loop
+// state and the descriptors are warp-uniform; inside the same asm statement
+// elect.sync picks the one lane that issues each MMA or commit.
+template <int MODE>
+__device__ __forceinline__ void mma_el(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (split_elem_bytes(MODE) == 4) {
+    asm volatile(
+        "{\n .reg .pred p, e;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p, e;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit_el(uint64_t* bar) {
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(smem_addr(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* r) {
@@ -900,7 +932,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     // the region's drain, and hands over the column blocks it finalises.  Both
     // wait for every A stage and release it (a_empty counts both).
     const int r_me = warp == kMmaWarp ? 0 : 1;
-    if (lane == 0 && r_me < P.issuers) {
+    if (r_me < P.issuers) {       // all 32 lanes: the loop state stays warp-uniform
       const int fmt = MODE == BO_PREC_FP16X3 ? 0 : MODE == BO_PREC_BF16X3 ? 1 : 2;
       const uint32_t a_base = smem_addr(sa), b_base = smem_addr(sb);
       bool ok = true;
@@ -923,17 +955,17 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
           uint32_t packed = 0;      // resident byte offset of chunk c's piece
           for (int c = 0; c < chunks && ok; ++c) {
             const int s = sa_i;
-            if (!(ok = mbar_wait(&a_full[s], pha, abort_flag, status))) break;
+            if (!(ok = warp_wait(&a_full[s], pha, abort_flag, status))) break;
             tc_fence_after();
             if (c == 0) {           // the buffer's previous tile has been drained
-              if (!(ok = mbar_wait(&acc_empty[as], (fill2[as] & 1u) ^ 1u, abort_flag, status))) break;
+              if (!(ok = warp_wait(&acc_empty[as], (fill2[as] & 1u) ^ 1u, abort_flag, status))) break;
               ++fill2[as];
               tc_fence_after();
             }
             const int r0 = c * cw, wd = n_pad - r0;
             const uint32_t part_bytes = (uint32_t)((wd >> 3) * 512);
             const int slot = P.b_resident ? c : tb;
-            if (!(ok = mbar_wait(&b_full[slot], P.b_resident ? 0u : phb, abort_flag, status))) break;
+            if (!(ok = warp_wait(&b_full[slot], P.b_resident ? 0u : phb, abort_flag, status))) break;
             tc_fence_after();
             const uint64_t ad0 = smem_desc(a_base + (uint32_t)(s * parts * kPartBytes), 128, 512);
             const uint64_t bd0 =
@@ -943,23 +975,23 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
             const uint32_t first = c > 0 ? 1u : 0u;
             if (parts == 2) {
               const uint64_t pbo = (uint64_t)(part_bytes >> 4), pao = (uint64_t)(kPartBytes >> 4);
-              mma<MODE>(dcol, ad0, bd0 + pbo, idesc, first);
-              mma<MODE>(dcol, ad0 + 16, bd0 + pbo + 16, idesc, 1u);
-              mma<MODE>(dcol, ad0 + pao, bd0, idesc, 1u);
-              mma<MODE>(dcol, ad0 + pao + 16, bd0 + 16, idesc, 1u);
-              mma<MODE>(dcol, ad0, bd0, idesc, 1u);
-              mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
+              mma_el<MODE>(dcol, ad0, bd0 + pbo, idesc, first);
+              mma_el<MODE>(dcol, ad0 + 16, bd0 + pbo + 16, idesc, 1u);
+              mma_el<MODE>(dcol, ad0 + pao, bd0, idesc, 1u);
+              mma_el<MODE>(dcol, ad0 + pao + 16, bd0 + 16, idesc, 1u);
+              mma_el<MODE>(dcol, ad0, bd0, idesc, 1u);
+              mma_el<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
             } else {
-              mma<MODE>(dcol, ad0, bd0, idesc, first);
-              mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
+              mma_el<MODE>(dcol, ad0, bd0, idesc, first);
+              mma_el<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
             }
             packed += part_bytes * (uint32_t)parts;
             if (!P.b_resident) {
-              mma_commit(&b_empty[tb]);
+              mma_commit_el(&b_empty[tb]);
               if (++tb == P.b_slots) { tb = 0; phb ^= 1; }
             }
-            mma_commit(&a_empty[s]);
-            if (c + 1 == chunks) mma_commit(&acc_full[as * 16 + c]);   // the region is final
+            mma_commit_el(&a_empty[s]);
+            if (c + 1 == chunks) mma_commit_el(&acc_full[as * 16 + c]);   // the region is final
             if (++sa_i == SA) { sa_i = 0; pha ^= 1; }
           }
         }
@@ -978,7 +1010,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         uint32_t packed = 0;        // resident byte offset of piece q
         for (int c = 0; c < chunks && ok; ++c) {
           const int s = sa_i;
-          if (!(ok = mbar_wait(&a_full[s], pha, abort_flag, status))) break;
+          if (!(ok = warp_wait(&a_full[s], pha, abort_flag, status))) break;
           tc_fence_after();
           const uint64_t ad0 = smem_desc(a_base + (uint32_t)(s * parts * kPartBytes), 128, 512);
           for (int r = 0; r < 2 && ok; ++r) {
@@ -996,11 +1028,11 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
             if (mine) {
               if (c == 0) {           // first write to this region since its last drain
                 uint32_t& f = P.acc_stages == 2 ? fill2[as] : fill;
-                if (!(ok = mbar_wait(&acc_empty[as + r], (f & 1u) ^ 1u, abort_flag, status))) break;
+                if (!(ok = warp_wait(&acc_empty[as + r], (f & 1u) ^ 1u, abort_flag, status))) break;
                 ++f;
                 tc_fence_after();
               }
-              if (!(ok = mbar_wait(&b_full[slot], P.b_resident ? 0u : phb, abort_flag, status))) break;
+              if (!(ok = warp_wait(&b_full[slot], P.b_resident ? 0u : phb, abort_flag, status))) break;
               tc_fence_after();
               // descriptors advance by address >> 4: +16 is the next 16-element K step
               const uint64_t bd0 = smem_desc(b_st, 128, 512);
@@ -1010,31 +1042,31 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
               if (parts == 2) {
                 // products (hi, lo), (lo, hi), (hi, hi): small terms first
                 const uint64_t pbo = (uint64_t)(part_bytes >> 4), pao = (uint64_t)(kPartBytes >> 4);
-                mma<MODE>(dcol, ad0, bd0 + pbo, idesc, first);
-                mma<MODE>(dcol, ad0 + 16, bd0 + pbo + 16, idesc, 1u);
-                mma<MODE>(dcol, ad0 + pao, bd0, idesc, 1u);
-                mma<MODE>(dcol, ad0 + pao + 16, bd0 + 16, idesc, 1u);
-                mma<MODE>(dcol, ad0, bd0, idesc, 1u);
-                mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
+                mma_el<MODE>(dcol, ad0, bd0 + pbo, idesc, first);
+                mma_el<MODE>(dcol, ad0 + 16, bd0 + pbo + 16, idesc, 1u);
+                mma_el<MODE>(dcol, ad0 + pao, bd0, idesc, 1u);
+                mma_el<MODE>(dcol, ad0 + pao + 16, bd0 + 16, idesc, 1u);
+                mma_el<MODE>(dcol, ad0, bd0, idesc, 1u);
+                mma_el<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
               } else {
-                mma<MODE>(dcol, ad0, bd0, idesc, first);
-                mma<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
+                mma_el<MODE>(dcol, ad0, bd0, idesc, first);
+                mma_el<MODE>(dcol, ad0 + 16, bd0 + 16, idesc, 1u);
               }
               if (!P.b_resident) {
-                mma_commit(&b_empty[slot]);
+                mma_commit_el(&b_empty[slot]);
                 if (++tb == my_size) { tb = 0; phb ^= 1; }
               }
             }
           }
           if (!ok) break;
-          mma_commit(&a_empty[s]);
-          if (((c * cw) >> 8) == r_me) mma_commit(&acc_full[as * 16 + c]);  // block c is final
+          mma_commit_el(&a_empty[s]);
+          if (((c * cw) >> 8) == r_me) mma_commit_el(&acc_full[as * 16 + c]);  // block c is final
           if (++sa_i == SA) { sa_i = 0; pha ^= 1; }
         }
       }
       }
       // every MMA of this CTA has completed before TMEM is released (issuer 0 waits for both)
-      mma_commit(drain);
+      mma_commit_el(drain);
       if (r_me == 0) {
         unsigned long long t0 = now_ns();
         while (!mbar_test(drain, 0) && now_ns() - t0 < kWaitNs) {
