@@ -298,11 +298,15 @@ __device__ __forceinline__ void acquire_body(const AcqDev& v, const PassArgs& a,
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) acquire_kernel(AcqDev v, PassArgs a) {
+  __shared__ double red[kThreads / 32 + 1];
   pdl_wait();                 // the prediction pass has completed (dependent launch)
+  // the variance sum: the prediction CTAs' sums added in CTA order (the same
+  // value in every block), or a given total
+  const double sum_var = v.var_parts ? block_sum_partials(v.var_parts, v.n_var_parts, red) : *v.sum_var;
   if constexpr (sizeof(T) == 4)
-    acquire_body_f32(v, a, blockIdx.x, gridDim.x, *v.sum_var);
+    acquire_body_f32(v, a, blockIdx.x, gridDim.x, sum_var);
   else
-    acquire_body<T>(v, a, blockIdx.x, gridDim.x, *v.sum_var);
+    acquire_body<T>(v, a, blockIdx.x, gridDim.x, sum_var);
 }
 
 // Many spaces in one launch: block b serves item block_item[b] as its
@@ -361,7 +365,9 @@ int launch_acquire(const DevView& v, const PassArgs& a, cudaStream_t s) {
   ad.var = v.var;
   ad.visited = v.visited;
   ad.N = v.N;
-  ad.sum_var = &v.stats->sum_var;
+  ad.sum_var = nullptr;
+  ad.var_parts = v.partial;
+  ad.n_var_parts = v.precision == BO_PREC_FP64 ? predict_f64_grid(v, a.n) : predict_tc_grid(v);
   ad.var_s = &v.stats->var_s;
   ad.status_in = &v.stats->status;
   ad.partial = v.acq_partial;

@@ -23,9 +23,9 @@ enum AfId { kEI = 0, kPI = 1, kLCB = 2 };
 
 // Device-side scalars of one space.
 struct DevStats {
-  double sum_var;            // sum of posterior variances of the last prediction pass
+  double sum_var;            // variance sum of the last pass with the acquisition as the prediction's tail
   double var_s;              // contextual-variance baseline (set by the first pass)
-  unsigned int k1_done;      // last-block counters (reset by the last block)
+  unsigned int k1_done;      // grid-barrier and last-block counters (reset by the last block)
   unsigned int k2_done;
   int32_t status;            // sticky BO_ERR_* of observation updates
   int32_t pad;
@@ -201,7 +201,11 @@ struct AcqDev {
   const void* var;           // [N] posterior variance
   const uint32_t* visited;   // [ceil(N/32)]
   int64_t N;
-  const double* sum_var;     // sum of variances over the non-evaluated candidates
+  const double* sum_var;     // sum of variances over the non-evaluated candidates (when var_parts is NULL)
+  // or: the prediction pass's per-CTA variance sums, which every acquisition
+  // block adds in the same fixed order (no last-CTA step in the prediction)
+  const double* var_parts = nullptr;
+  int n_var_parts = 0;
   double* var_s;             // contextual-variance baseline (written on a first pass)
   const int32_t* status_in;  // status folded into the result, or NULL
   TopEntry* partial;         // [max_blocks][3][3] scratch
@@ -285,6 +289,10 @@ int launch_observe_batch(const ObsItem* items, int count, const ObsBlock* blocks
                          const VisitItem* visits, int n_visits, bool tc, cudaStream_t s);
 int launch_predict_f64(const DevView& v, int n, int64_t n_unvisited, cudaStream_t s);
 int launch_predict_tc(const DevView& v, int n, int64_t n_unvisited, cudaStream_t s);
+// CTAs of a single-space prediction launch: each writes one per-CTA variance
+// sum to DevView::partial, which the acquisition adds up.
+int predict_f64_grid(const DevView& v, int n);
+int predict_tc_grid(const DevView& v);
 // The tensor-core pass with the acquisition of `a` as its tail (one
 // cooperative launch writing the pass result); -2 if the device does not
 // launch it cooperatively (then predict + acquire as two launches).

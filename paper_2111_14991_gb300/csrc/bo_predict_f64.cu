@@ -10,8 +10,8 @@
 // and inside it each 16-column group skips the slices above its own
 // diagonal and the columns beyond n.
 // Each CTA also writes the sum of the variances of its non-evaluated
-// candidates; the last CTA to finish adds those partial sums in block order
-// (deterministic) into stats->sum_var for the exploration factor (Sec. III-F).
+// candidates; the acquisition adds those partial sums in block order
+// (deterministic) for the exploration factor (Sec. III-F).
 #include "bo_internal.h"
 
 namespace bo {
@@ -88,7 +88,6 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
   uint8_t* Xc = reinterpret_cast<uint8_t*>(meta + 2 * d + 1);
   uint8_t* Cc = Xc + d * n_pad;
   __shared__ double red[kThreads / 32 + 1];
-  __shared__ bool s_last;
 
   const int tid = threadIdx.x;
   const int64_t row0 = (int64_t)blockIdx.x * BM;
@@ -201,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
     }
   }
   pdl_trigger();                           // the acquisition may be launched (it waits for completion)
-  // block sum of variances in a fixed order
+  // block sum of variances in a fixed order; the acquisition adds the blocks' sums
   for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
   if ((tid & 31) == 0) red[tid >> 5] = vsum;
   __syncthreads();
@@ -209,18 +208,6 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
     double t = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) t += red[w];
     v.partial[blockIdx.x] = t;
-    __threadfence();
-    const unsigned int done = atomicAdd(&v.stats->k1_done, 1u);
-    s_last = (done == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    const double t = block_sum_partials(v.partial, (int)gridDim.x, red);
-    if (tid == 0) {
-      v.stats->sum_var = t;
-      v.stats->k1_done = 0;
-    }
   }
 }
 
@@ -238,7 +225,7 @@ int launch_bm(const DevView& v, int n, cudaStream_t s) {
   const size_t sm = smem_bytes<BM, TAB>(v.d, n_pad, v.sqd_total);
   static size_t configured[kMaxDevices] = {};
   if (!ensure_dynamic_smem((const void*)predict_f64_kernel<BM, TAB>, configured, sm)) return -1;
-  const int grid = (int)(v.N_pad / BM);
+  const int grid = predict_f64_grid(v, n);
   if (grid > v.max_partials) return -1;
   return launch_ex(predict_f64_kernel<BM, TAB>, dim3(grid), dim3(kThreads), sm, s, pdl_enabled(), v, n, n_pad) ==
                  cudaSuccess
@@ -247,6 +234,8 @@ int launch_bm(const DevView& v, int n, cudaStream_t s) {
 }
 
 }  // namespace
+
+int predict_f64_grid(const DevView& v, int n) { return (int)(v.N_pad / (n <= 256 ? 64 : 32)); }
 
 int launch_predict_f64(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStream_t s) {
   if (n < 1) return -1;

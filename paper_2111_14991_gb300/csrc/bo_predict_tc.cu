@@ -27,16 +27,18 @@
 //                space's own d coordinates), adds its share of k* . alpha,
 //                splits it and stores it in the K-major core-matrix layout.
 //                The next tile's candidate codes are fetched while the
-//                current tile is computed.
+//                current tile is computed (the first tile's before the
+//                dependent wait).
 //   warps 16-19  drain the accumulator (TMEM lane = row): sum acc_k^2 q_k
 //                (q of the space in shared memory) and write var; add a
 //                row's four quarter sums of k* . alpha (handed over in shared
-//                memory) and write mu.  A 256-column region is final once the
-//                chunk writing its last column block completes, so it is
-//                drained then and handed back: the next tile's first MMAs into
-//                a region wait only for that region.  With n <= 256 the
-//                accumulator is double-buffered.
-//   warps 20, 22 issue the MMAs (one thread each): warp 20 for accumulator
+//                memory) and write mu.  Each 32-column block is drained as
+//                soon as the chunk that completes it has run, and a 256-column
+//                region is handed back after its last block: the next tile's
+//                first MMAs into a region wait only for that region.  With
+//                n <= 256 the accumulator is double-buffered.
+//   warps 20, 22 issue the MMAs (the whole warp runs the loop, one elected
+//                lane issues each MMA and commit): warp 20 for accumulator
 //                columns 0-255 (and owns the TMEM allocation), warp 22 for
 //                columns 256-511 when n > 256, so that the two halves'
 //                instruction streams overlap.
@@ -88,7 +90,7 @@ struct TcParams {
   const int* seg_begin;
   double* seg_part;          // batch > 0: [segment][4] variance sums of the epilogue warps
   double* partial;           // batch == 0: per-CTA variance sums
-  DevStats* stats;           // batch == 0: last-block total; status word of the launch
+  DevStats* stats;           // batch == 0: the fused tail's counters; status word of the launch
   int32_t* status;
   int batch;
   int cw, parts, stages_a;
@@ -279,27 +281,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 __host__ __device__ __forceinline__ uint32_t instr_desc(int fmt, int m, int n) {
   return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(m >> 4) << 24);
-}
-
-template <int MODE>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if constexpr (split_elem_bytes(MODE) == 4) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_addr(bar))
-               : "memory");
 }
 
 // The MMA-issuing warps run their loops with all 32 lanes, so that the loop
@@ -630,7 +611,6 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SA + 2 * kMaxBSlots + kAccBars + 11);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ double red[4];   // per epilogue warp
-  __shared__ bool s_last;
   int32_t* status = P.status;
 
   // ---- setup: barriers, TMEM
@@ -667,6 +647,29 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     if (P.parts == 2) l2_prefetch_share(S.llo, lbytes, blockIdx.x, gridDim.x);
     l2_prefetch_share(S.codes, (size_t)S.d * (size_t)S.N_pad, blockIdx.x, gridDim.x);
   }
+  // the producers' candidate codes, four per word: the first tile's are read
+  // here, before the dependent wait, while the update may still be running
+  // (the codes and value tables are static: the update writes neither), with
+  // the value-table entries they select pulled into L1; each later tile's are
+  // fetched during the tile before it
+  uint32_t code_next[(DMAX + 3) / 4];
+#pragma unroll
+  for (int p = 0; p < (DMAX + 3) / 4; ++p) code_next[p] = 0u;
+  if (warp < kProducerWarps) {
+    Work w0;
+    if (work_begin(P, w0)) {
+      const TcSess& S0 = sess_of(P, w0.sess);
+      const int64_t cand0 = (int64_t)w0.tile * kRows + (threadIdx.x & (kRows - 1));
+#pragma unroll
+      for (int p = 0; p < DMAX; ++p)
+        if (p < S0.d) {
+          const uint32_t code = S0.codes[(int64_t)p * S0.N_pad + cand0];
+          code_next[p >> 2] |= code << (8 * (p & 3));
+          float t;
+          asm volatile("ld.global.ca.f32 %0, [%1];" : "=f"(t) : "l"(S0.vtab32 + p * 256 + code));
+        }
+    }
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -687,12 +690,8 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     int s = 0, ks = -1, prev = -1, tile_it = 0;
     uint32_t ph = 0;                             // ring slot and its phase
     int n_pad = 0, chunks = 0, d = 0, ds = 0, gstride = 0;
-    int64_t N_pad = 0;
-    const uint8_t* codes = nullptr;
     const float* vt = nullptr;
     uint32_t xs = xs_base;
-    uint32_t code_next[(DMAX + 3) / 4];         // the next tile's codes, four per word
-    bool have_next = false;
     Work w;
     for (bool more = work_begin(P, w); more && ok; more = work_next(P, w), ++tile_it) {
       if (w.sess != prev) {                      // next space: its coordinates, once copied in
@@ -706,29 +705,24 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         n_pad = S.n_pad;
         chunks = S.chunks;
         d = S.d;
-        N_pad = S.N_pad;
-        codes = S.codes;
         vt = S.vtab32;
         ds = S.ds;
         gstride = 32 * (ds + 2);
         xs = xs_base + (uint32_t)((ks % XB) * P.x_buf_bytes);
         if (!(ok = mbar_wait(&xs_full[ks % XB], (uint32_t)((ks / XB) & 1), abort_flag, status))) break;
       }
-      const int64_t cand = (int64_t)w.tile * kRows + row;
       // mu = k* . alpha: two packed FP32 sums over groups of 4 chunks, folded
       // into a compensated (hi, lo) pair by Knuth's TwoSum after each group
       uint64_t m2 = 0ull, mhi = 0ull, mlo = 0ull;
       {
-        // this tile's candidate codes: prefetched during the previous tile, except for the first
-        uint32_t cc[DMAX];
+        // this tile's candidate coordinates, from the codes in code_next
+        uint64_t xcp[DMAX];                    // candidate coordinate, twice per word
 #pragma unroll
         for (int p = 0; p < DMAX; ++p)
-          cc[p] = have_next ? (code_next[p >> 2] >> (8 * (p & 3))) & 0xFFu
-                            : (p < d ? (uint32_t)codes[(int64_t)p * N_pad + cand] : 0u);
+          xcp[p] = dup2(p < d ? vt[p * 256 + ((code_next[p >> 2] >> (8 * (p & 3))) & 0xFFu)] : 0.0f);
         {
           Work wn = w;
-          have_next = work_next(P, wn);
-          if (have_next) {
+          if (work_next(P, wn)) {
             const TcSess& Sn = sess_of(P, wn.sess);
             const int64_t cn = (int64_t)wn.tile * kRows + row;
             const int dn = Sn.d;
@@ -741,9 +735,6 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
               if (p < dn) code_next[p >> 2] |= (uint32_t)cp[(int64_t)p * Nn + cn] << (8 * (p & 3));
           }
         }
-        uint64_t xcp[DMAX];                    // candidate coordinate, twice per word
-#pragma unroll
-        for (int p = 0; p < DMAX; ++p) xcp[p] = dup2(p < d ? vt[p * 256 + cc[p]] : 0.0f);
         for (int c = 0; c < chunks && ok; ++c) {
           const int j0 = c * cw + quarter * jq;
           // K* for this thread's observations, computed before waiting for the ring slot
@@ -863,21 +854,18 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
         mu = S.mu;
         if (!(ok = mbar_wait(&xs_full[ks % XB], (uint32_t)((ks / XB) & 1), abort_flag, status))) break;
       }
-      // a 256-column region of the accumulator is final once the chunk that
-      // writes its last column block completes (the issuer owning the region
-      // signals that block's barrier): drain the region then and hand it back
+      // column block c (32 columns) of the accumulator is final once chunk c
+      // completes (the issuer owning its region commits that block's barrier);
+      // a 256-column region is handed back once its last block is drained
       const int as = it % P.acc_stages;
       const uint32_t lane_base = tmem + (uint32_t)(as * P.tmem_cols) + ((uint32_t)(e * 32) << 16);
       uint64_t s2p = 0ull;                       // two columns per packed word
-      // (two issuers, n > 256: every column block is signalled as it becomes
-      // final, so region 0 drains while region 1 is still being accumulated)
-      const bool per_block = P.issuers == 2;
+      // (every column block is signalled as it becomes final, so earlier
+      // blocks drain while later chunks are still being accumulated)
       for (int c = 0; c < chunks && ok; ++c) {
-        if (per_block || c == 0) {
-          const int c_end = per_block ? c : min(kPieceRows, n_pad) / CW - 1;
-          if (!(ok = mbar_wait(&acc_full[as * 16 + c_end], (par[as] >> c_end) & 1u, abort_flag, status)))
-            break;
-          par[as] ^= 1u << c_end;
+        {
+          if (!(ok = mbar_wait(&acc_full[as * 16 + c], (par[as] >> c) & 1u, abort_flag, status))) break;
+          par[as] ^= 1u << c;
           tc_fence_after();
         }
         const int k0 = c * CW;
@@ -991,7 +979,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
               if (++tb == P.b_slots) { tb = 0; phb ^= 1; }
             }
             mma_commit_el(&a_empty[s]);
-            if (c + 1 == chunks) mma_commit_el(&acc_full[as * 16 + c]);   // the region is final
+            mma_commit_el(&acc_full[as * 16 + c]);   // column block c is final
             if (++sa_i == SA) { sa_i = 0; pha ^= 1; }
           }
         }
@@ -1154,7 +1142,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     }
   }
 
-  // ---- teardown: TMEM release; one space: per-CTA variance sum, last-block total
+  // ---- teardown: TMEM release; one space: per-CTA variance sum
   pdl_trigger();           // the acquisition may be launched (it waits for completion)
   for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
   if (warp >= kEpiWarp0 && warp < kMmaWarp && lane == 0) red[warp - kEpiWarp0] = vsum;
@@ -1170,21 +1158,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_tc_kernel(const __grid_co
     acquisition_tail(P, red[0] + red[1] + red[2] + red[3], reinterpret_cast<unsigned long long*>(smem));
     return;
   }
-  if (threadIdx.x == 0) {
-    P.partial[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
-    __threadfence();
-    const unsigned int done = atomicAdd(&P.stats->k1_done, 1u);
-    s_last = (done == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    const double t = block_sum_partials(P.partial, (int)gridDim.x, reinterpret_cast<double*>(smem));
-    if (threadIdx.x == 0) {
-      P.stats->sum_var = t;
-      P.stats->k1_done = 0;
-    }
-  }
+  if (threadIdx.x == 0) P.partial[blockIdx.x] = red[0] + red[1] + red[2] + red[3];   // the acquisition adds them
 }
 
 // dimension buckets: the distance loop runs over DMAX zero-padded coordinates
@@ -1371,7 +1345,7 @@ int launch_single(const DevView& v, int n, const PassArgs* a, cudaStream_t s) {
   const size_t smem = plan_smem(P, v.precision, P.s0.n_pad, dmax, true,
                                 shape_for(v.precision, v.nu, dmax, P.s0.n_pad, false));
   if (!smem) return -1;
-  const int grid = std::min(P.s0.num_tiles, num_sms());
+  const int grid = predict_tc_grid(v);
   if (grid > v.max_partials) return -1;
   if (a) {
     if (grid > v.max_acq_blocks || a->result_slot < 0 || a->result_slot >= v.max_results) return -1;
@@ -1385,6 +1359,8 @@ int launch_single(const DevView& v, int n, const PassArgs* a, cudaStream_t s) {
 }
 
 }  // namespace
+
+int predict_tc_grid(const DevView& v) { return std::min((int)(v.N_pad / kRows), num_sms()); }
 
 int launch_predict_tc(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStream_t s) {
   return launch_single(v, n, nullptr, s);

@@ -40,6 +40,7 @@ def run(SA, b_slots, n_pad, shared_ring=False, tiles=4, cw=32, seed=0, max_steps
     rnd = random.Random(seed)
     chunks = n_pad // cw
     issuers = 2 if n_pad > 256 else 1
+    stages = 2 if n_pad <= 256 else 1        # accumulator buffers (2 x n_pad columns fit in TMEM)
     if issuers == 1 or shared_ring:
         ring = [b_slots, 0] if not shared_ring else [b_slots, b_slots]
     else:
@@ -85,8 +86,9 @@ def run(SA, b_slots, n_pad, shared_ring=False, tiles=4, cw=32, seed=0, max_steps
     def issuer(rme):
         mine = slot_seq(rme)
         sa = pha = 0
-        fill = 0
+        fill = [0, 0]                 # tiles started per accumulator buffer
         for t in range(tiles):
+            buf = t % stages
             for c in range(chunks):
                 s = sa
                 while not a_full[s].done(pha):
@@ -94,34 +96,30 @@ def run(SA, b_slots, n_pad, shared_ring=False, tiles=4, cw=32, seed=0, max_steps
                 if rme in pieces(c, cw, n_pad):
                     _, _, slot, ph = next(mine)
                     if c == 0:
-                        while not acc_empty[rme].done((fill & 1) ^ 1):
+                        while not acc_empty[buf + rme].done((fill[buf] & 1) ^ 1):
                             yield
-                        fill += 1
+                        fill[buf] += 1
                     while not b_full[slot].done(ph):
                         yield
                     b_empty[slot].arrive()
                 a_empty[s].arrive()
-                if issuers == 1:
-                    if c + 1 == chunks:
-                        acc_full[c].arrive()
-                elif (c * cw) >> 8 == rme:
-                    acc_full[c].arrive()
+                if issuers == 1 or (c * cw) >> 8 == rme:
+                    acc_full[buf * 16 + c].arrive()      # column block c is final
                 sa = (sa + 1) % SA
                 pha ^= sa == 0
 
     def epilogue():
-        par = 0
+        par = [0, 0]
         for t in range(tiles):
+            buf = t % stages
             for c in range(chunks):
-                if issuers == 2 or c == 0:
-                    cend = c if issuers == 2 else min(256, n_pad) // cw - 1
-                    while not acc_full[cend].done((par >> cend) & 1):
-                        yield
-                    par ^= 1 << cend
+                while not acc_full[buf * 16 + c].done((par[buf] >> c) & 1):
+                    yield
+                par[buf] ^= 1 << c
                 kend = c * cw + cw
                 if kend == n_pad or kend % 256 == 0:
                     for _ in range(4):
-                        acc_empty[(kend - 1) >> 8].arrive()
+                        acc_empty[buf + ((kend - 1) >> 8)].arrive()
             while not mu_full[t & 1].done((t >> 1) & 1):
                 yield
             mu_empty[t & 1].arrive()
