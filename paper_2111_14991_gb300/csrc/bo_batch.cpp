@@ -235,10 +235,7 @@ int bo_batch_observe(bo_batch* b, const int64_t* idx, const double* values, int3
           ObsItem& it = items[n_items++];
           it.v = s->v;
           it.n = nb;
-          it.idx = idx[i];
-          it.y_raw = values[i];
-          it.y_mean = mean;
-          it.inv_std = 1.0 / sd;
+          make_obs_new(s, idx[i], values[i], mean, sd, &it.o);
           n_before.push_back(nb);
         } else if (rc == BO_OK) {
           visits[n_visits].visited = s->v.visited;

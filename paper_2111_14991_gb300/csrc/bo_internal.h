@@ -48,6 +48,7 @@ struct DevView {
   int n_max;                 // capacity in fitted observations (multiple of 32)
   int precision;             // BO_PREC_*
   double nu, lengthscale, jitter;
+  double kcoef;              // sqrt(2 nu) / lengthscale, formed once on the host
 
   const uint8_t* codes;      // [d][N_pad] value index per parameter, parameter-major
   const double* vtab64;      // [d][256] normalized values
@@ -84,6 +85,7 @@ struct DevView {
   double* kvec;              // [n_max] update scratch
   double* lvec;              // [n_max]
   double* wvec;              // [n_max]
+  double* upart;             // [update_part_count(n_max)]: the l and w phases' block shares of the pivot sums
 
   DevStats* stats;
   TopEntry* acq_partial;     // [max_acq_blocks][3][3]
@@ -261,12 +263,30 @@ struct AcqItem {
 };
 
 // One observation update of a batch (the arguments of the single-space launch).
+// The new observation as the update reads it: its index and value, the fit's
+// standardization, and the point's value indices, coordinates and distance
+// table metadata, all formed on the host (the k phase starts without a chain
+// of dependent loads).
+struct ObsNew {
+  long long idx;
+  double y_raw, y_mean, inv_std;
+  int32_t a[BO_MAX_PARAMS];     // value index of parameter p
+  int32_t off[BO_MAX_PARAMS];   // offset of parameter p's table of squared differences
+  int32_t m[BO_MAX_PARAMS];     // value count of parameter p
+  double x[BO_MAX_PARAMS];      // coordinate of parameter p
+};
 struct ObsItem {
   DevView v;
   int n;                     // observations fitted before this one
-  long long idx;
-  double y_raw, y_mean, inv_std;
+  ObsNew o;
 };
+// Doubles of DevView::upart for n_max observations: three shares (l.l, k.a,
+// k.b) per 8-row block of the l phase, two (w.(y - y0), w.1) per 32 x 64
+// block of the w phase.
+inline size_t update_part_count(int n_max) {
+  const size_t nl = ((size_t)n_max + 7) / 8, nw = (((size_t)n_max + 31) / 32) * (((size_t)n_max + 63) / 64);
+  return 3 * nl + 2 * nw;
+}
 struct ObsBlock {
   int item, local;           // space and its block index within one phase
 };
@@ -279,8 +299,7 @@ struct VisitItem {
 // Self-tests of the bounded device waits (each returns 1 when launched).
 int launch_selftest_mbar(int32_t* status, int* abort_flag, cudaStream_t s);
 int launch_selftest_grid(DevStats* st, cudaStream_t s);
-int launch_observe_update(bool cooperative, const DevView& v, int n, int64_t idx, double y_raw, double y_mean,
-                          double y_std, cudaStream_t s);
+int launch_observe_update(bool cooperative, const DevView& v, int n, const ObsNew& o, cudaStream_t s);
 int launch_set_visited(const DevView& v, int64_t idx, cudaStream_t s);
 // Block tables of the batched update phases k, l, w, beta (concatenated) for spaces with
 // n[i] observations fitted before their new one; counts[] receives each phase's block count.

@@ -54,6 +54,23 @@ uint64_t splitmix64_next(uint64_t& state) {
   return z ^ (z >> 31);
 }
 
+void make_obs_new(const bo_space* s, int64_t idx, double y, double y_mean, double y_std, ObsNew* o) {
+  *o = ObsNew{};
+  o->idx = (long long)idx;
+  o->y_raw = y;
+  o->y_mean = y_mean;
+  o->inv_std = 1.0 / y_std;
+  int off = 0;   // the squared-difference tables lie parameter after parameter, m_p^2 entries each
+  for (int p = 0; p < s->d; ++p) {
+    const int a = s->codes[(size_t)p * s->N + idx];
+    o->a[p] = a;
+    o->x[p] = s->values[p][a];
+    o->off[p] = off;
+    o->m[p] = s->sizes[p];
+    off += s->sizes[p] * s->sizes[p];
+  }
+}
+
 }  // namespace host
 }  // namespace bo
 
@@ -260,8 +277,14 @@ int observe_impl(bo_space* s, int64_t idx, double value) {
   double mean = 0.0, sd = 1.0;
   int rc = observe_host(s, idx, value, &fit, &n_before, &mean, &sd);
   if (rc != BO_OK) return rc;
-  const int k = fit ? launch_observe_update(s->coop_update, s->v, n_before, idx, value, mean, sd, s->stream)
-                    : launch_set_visited(s->v, idx, s->stream);
+  int k = 0;
+  if (fit) {
+    ObsNew o;
+    make_obs_new(s, idx, value, mean, sd, &o);
+    k = launch_observe_update(s->coop_update, s->v, n_before, o, s->stream);
+  } else {
+    k = launch_set_visited(s->v, idx, s->stream);
+  }
   if (k < 0) return fail(BO_ERR_CUDA, "update launch failed");
   s->launches += k;
   return BO_OK;
@@ -477,6 +500,7 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   v.nu = D.nu;
   v.lengthscale = D.lengthscale;
   v.jitter = D.jitter;
+  v.kcoef = std::sqrt(2.0 * D.nu) / D.lengthscale;
   int num_sms = 152;
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, s->device);
   v.max_partials = (int)(N_pad / 32) + num_sms;
@@ -532,6 +556,7 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   TRY(dalloc_n(s, (size_t)n_alloc, &v.kvec));
   TRY(dalloc_n(s, (size_t)n_alloc, &v.lvec));
   TRY(dalloc_n(s, (size_t)8 * n_alloc, &v.wvec));
+  TRY(dalloc_n(s, update_part_count(n_alloc), &v.upart));
   TRY(dalloc_n(s, 1, &v.stats));
   TRY(dalloc_n(s, (size_t)v.max_acq_blocks * 9, &v.acq_partial));
   TRY(dalloc_n(s, (size_t)v.max_results, &v.results));

@@ -193,6 +193,9 @@ int cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 uint64_t splitmix64_next(uint64_t& state);
+// The new observation idx as the update kernels read it (value y, the fit's
+// mean and standard deviation after it).
+void make_obs_new(const bo_space* s, int64_t idx, double y, double y_mean, double y_std, bo::ObsNew* o);
 // The initial sample of bo_initial_design: `count` distinct valid-list indices
 // into out, drawn from rng (advanced); valid_of maps a flat (row-major)
 // configuration index to its valid-list index, or -1 when restricted.

@@ -27,10 +27,6 @@ __device__ __forceinline__ double matern64(double r, double nu, double c) {
   return nu == 1.5 ? (1.0 + t) * e : (1.0 + t + t * t * (1.0 / 3.0)) * e;
 }
 
-__device__ __forceinline__ double coord64(const DevView& v, int64_t idx, int p) {
-  return v.vtab64[p * 256 + v.codes[(int64_t)p * v.N_pad + idx]];
-}
-
 // Byte offset of element (row k, column j) of L^-1 in the chunked copy.
 // Chunk c holds columns [c*CW, (c+1)*CW) of rows k >= c*CW, in the K-major
 // no-swizzle core-matrix layout the tensor core reads: 8-row x 16-byte core
@@ -57,24 +53,23 @@ size_t lsplit_bytes(int n_max, int precision) {
 
 // --- K3a: X[n] = x(idx), y[n] = y, visited bit, k_j = k(|x - X_j|) --------------
 // (obs_record: the bookkeeping, by one block; obs_kj: one entry of k)
-__device__ __forceinline__ void obs_record(const DevView& v, int n, long long idx, double y_raw) {
+__device__ __forceinline__ void obs_record(const DevView& v, int n, const ObsNew& o) {
   if (threadIdx.x < v.d) {
-    const double c = sqrt(2.0 * v.nu) / v.lengthscale;
-    const double x = coord64(v, idx, threadIdx.x);
-    v.X[(size_t)n * v.d + threadIdx.x] = x;
-    v.Xc[(size_t)n * v.d + threadIdx.x] = v.codes[(int64_t)threadIdx.x * v.N_pad + idx];
-    if (v.xq) v.xq[xq_index(v.ds, n, threadIdx.x)] = (float)(x * (1.4426950408889634 * c));
+    const int p = threadIdx.x;
+    v.X[(size_t)n * v.d + p] = o.x[p];
+    v.Xc[(size_t)n * v.d + p] = (uint8_t)o.a[p];
+    if (v.xq) v.xq[xq_index(v.ds, n, p)] = (float)(o.x[p] * (1.4426950408889634 * v.kcoef));
   }
   if (threadIdx.x == 0) {
-    v.y[n] = y_raw;
-    atomicOr(&v.visited[idx >> 5], 1u << (idx & 31));
+    v.y[n] = o.y_raw;
+    atomicOr(&v.visited[o.idx >> 5], 1u << (o.idx & 31));
   }
 }
 
-// The new point's codes and coordinates and the table offsets, staged in
-// shared memory once per block, so that an entry of k needs one round of
-// loads (its observation's codes or coordinates, then the table entries)
-// instead of a chain of dependent global loads per parameter.
+// The new point's codes and coordinates and the table offsets (formed on the
+// host), staged in shared memory once per block, so that an entry of k needs
+// one round of loads (its observation's codes or coordinates, then the table
+// entries).
 struct KStage {
   int off[BO_MAX_PARAMS];      // table offset of parameter p (tabulated distances)
   int m[BO_MAX_PARAMS];        // value count of parameter p
@@ -82,20 +77,18 @@ struct KStage {
   double x[BO_MAX_PARAMS];     // the new point's coordinate of parameter p
 };
 
-__device__ __forceinline__ void k_stage(const DevView& v, long long idx, KStage& ks) {
+__device__ __forceinline__ void k_stage(const DevView& v, const ObsNew& o, KStage& ks) {
   for (int p = threadIdx.x; p < v.d; p += blockDim.x) {
-    ks.a[p] = v.codes[(int64_t)p * v.N_pad + idx];
-    ks.x[p] = v.vtab64[p * 256 + ks.a[p]];
-    if (v.sqd) {
-      ks.off[p] = v.sqd_meta[p];
-      ks.m[p] = v.sqd_meta[v.d + 1 + p];
-    }
+    ks.a[p] = o.a[p];
+    ks.x[p] = o.x[p];
+    ks.off[p] = o.off[p];
+    ks.m[p] = o.m[p];
   }
   __syncthreads();
 }
 
 __device__ __forceinline__ void obs_kj(const DevView& v, const KStage& ks, int j) {
-  const double c = sqrt(2.0 * v.nu) / v.lengthscale;
+  const double c = v.kcoef;
   double r2 = 0.0;
   if (v.sqd) {   // the prediction pass's arithmetic: a sum of tabulated squared differences
 #pragma unroll
@@ -112,34 +105,52 @@ __device__ __forceinline__ void obs_kj(const DevView& v, const KStage& ks, int j
   v.kvec[j] = matern64(sqrt(r2), v.nu, c);
 }
 
-__device__ __forceinline__ void obs_k_body(const DevView& v, int n, long long idx, double y_raw, int block) {
+__device__ __forceinline__ void obs_k_body(const DevView& v, int n, const ObsNew& o, int block) {
   __shared__ KStage ks;
   const int j = block * blockDim.x + threadIdx.x;
-  if (block == 0) obs_record(v, n, idx, y_raw);
-  k_stage(v, idx, ks);
+  if (block == 0) obs_record(v, n, o);
+  k_stage(v, o, ks);
   if (j < n) obs_kj(v, ks, j);
 }
 
-__global__ void obs_k_kernel(DevView v, int n, long long idx, double y_raw) {
-  obs_k_body(v, n, idx, y_raw, blockIdx.x);
-}
+__global__ void obs_k_kernel(DevView v, int n, const __grid_constant__ ObsNew o) { obs_k_body(v, n, o, blockIdx.x); }
 
 __device__ __forceinline__ double warp_sum(double x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
 
-// --- K3b: l = L^-1 k (warp per row) -------------------------------------------
+// --- K3b: l = L^-1 k (warp per row, 8 rows per block of 256) ----------------------
+// The block also writes its shares of three pivot sums over its rows i:
+// l_i^2, k_i a_i and k_i b_i, each added in row order (upart[3 block + q]);
+// the pivot phase adds the blocks' shares, so no single block reduces over n.
 __device__ __forceinline__ void obs_l_body(const DevView& v, int n, int block) {
-  const int warp = (block * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const double* row = v.linv + (size_t)warp * v.n_max;
-  double s = 0.0;
+  __shared__ double s_part[8][3];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = block * 8 + w;
+  double l = 0.0;
+  if (row < n) {
+    const double* r = v.linv + (size_t)row * v.n_max;
+    double s = 0.0;
 #pragma unroll 4
-  for (int j = lane; j <= warp; j += 32) s = fma(row[j], v.kvec[j], s);
-  s = warp_sum(s);
-  if (lane == 0) v.lvec[warp] = s;
+    for (int j = lane; j <= row; j += 32) s = fma(r[j], v.kvec[j], s);
+    l = warp_sum(s);
+    if (lane == 0) v.lvec[row] = l;
+  }
+  if (lane == 0) {
+    const bool tc = row < n && v.avec != nullptr;
+    s_part[w][0] = l * l;
+    s_part[w][1] = tc ? v.kvec[row] * v.avec[row] : 0.0;
+    s_part[w][2] = tc ? v.kvec[row] * v.bvec[row] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += s_part[q][threadIdx.x];
+    v.upart[3 * block + threadIdx.x] = t;
+  }
+  __syncthreads();   // s_part is reused by the block's next row group
 }
 
 __global__ void obs_l_kernel(DevView v, int n) { obs_l_body(v, n, blockIdx.x); }
@@ -147,6 +158,8 @@ __global__ void obs_l_kernel(DevView v, int n) { obs_l_body(v, n, blockIdx.x); }
 // --- K3c: partial w = L^-T l over row segments of 64 ---------------------------
 // Block (column block of 32, row segment of 64): lane = column, warp w sums
 // rows seg*64 + 8w .. +8 with all eight loads in flight; L^-1[i][j] = 0 for j > i.
+// w.(y - y0) and w.1 are linear in these row-segment sums, so each block also
+// writes its shares of both (upart[3 nl + 2 (by gx + bx) + q]).
 __device__ __forceinline__ void obs_w_body(const DevView& v, int n, int bx, int by) {
   __shared__ double part[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -167,11 +180,20 @@ __device__ __forceinline__ void obs_w_body(const DevView& v, int n, int bx, int 
   }
   part[w][lane] = s;
   __syncthreads();
-  if (w == 0 && j < n) {
+  if (w == 0) {
     double t = 0.0;
+    if (j < n) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) t += part[q][lane];
-    v.wvec[(size_t)by * v.n_max + j] = t;
+      for (int q = 0; q < 8; ++q) t += part[q][lane];
+      v.wvec[(size_t)by * v.n_max + j] = t;
+    }
+    const double ty = warp_sum(j < n ? t * (v.y[j] - v.y[0]) : 0.0);
+    const double t1 = warp_sum(t);
+    if (lane == 0) {
+      const int nl = (n + 7) / 8, gx = (n + 31) / 32;
+      v.upart[3 * nl + 2 * (by * gx + bx)] = ty;
+      v.upart[3 * nl + 2 * (by * gx + bx) + 1] = t1;
+    }
   }
 }
 
@@ -190,20 +212,28 @@ __global__ void obs_w_kernel(DevView v, int n) { obs_w_body(v, n, blockIdx.x, bl
 // (the same for b with 1 - k.b), so the whole update of beta and alpha is O(n).
 
 // The pivot and every scalar of the new row follow from five sums over the
-// previous rows, formed in one block reduction (FP64 latency is long on this
-// GPU: one reduction and one pass over the row keep the serial chain short):
-//   l.l,  w.(y - y0),  w.1,  k.a,  k.b   and   max |w|   (w = L^-T l)
+// previous rows and max |w| (w = L^-T l):
+//   l.l,  w.(y - y0),  w.1,  k.a,  k.b   (shares written by the l and w phases)
 // d^2 = k(0) + jitter - l.l;  the new row is [-w / d, 1 / d], so
 //   u_n = row . (y - y0) = ((y_n - y0) - w.(y - y0)) / d,  e_n = (1 - w.1) / d,
 //   g_a = ((y_n - y0) - k.a) / d^2,  g_b = (1 - k.b) / d^2,
 // and the row's largest magnitude, for the split copy's scale, is max|w| / d or 1 / d.
-__device__ __forceinline__ void obs_finish_body(const DevView& v, int n, double y_mean, double inv_std) {
-  __shared__ double red[6][32];
+// FP64 is a narrow unit on this GPU (one warp instruction occupies it for ~64
+// cycles), so no block reduces over n: each block adds the phases' block
+// shares (warp q adds sum q in block order: the same value in every block),
+// takes max |w| as an integer maximum of the bit patterns (non-negative doubles
+// order as their bits), forms the scalars in one thread, and writes entries
+// j = slice + nslices t of the row (slice 0 of nslices also the bookkeeping).
+__device__ __forceinline__ void obs_finish_body(const DevView& v, int n, double y_mean, double inv_std, int slice,
+                                                int nslices) {
+  __shared__ double s_sum[5];  // l.l, k.a, k.b, w.(y - y0), w.1
+  __shared__ unsigned long long s_wmax;
   __shared__ double s_sc[8];   // dinv, d2, u_n, e_n, g_a, g_b, amax
   __shared__ float s_scale;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool tc = v.precision != BO_PREC_FP64;
   const int nseg = (n + 63) / 64;
+  const int nl = (n + 7) / 8, nw = ((n + 31) / 32) * nseg;
   const double y0 = v.y[0];
   auto w_of = [&](int j) {
     double w = 0.0;
@@ -212,57 +242,54 @@ __device__ __forceinline__ void obs_finish_body(const DevView& v, int n, double 
       if (s < nseg) w += v.wvec[(size_t)s * v.n_max + j];
     return w;
   };
-  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // l.l, w.(y-y0), w.1, k.a, k.b, max|w|
-  for (int j = tid; j < n; j += blockDim.x) {
-    const double l = v.lvec[j], w = w_of(j);
-    acc[0] = fma(l, l, acc[0]);
-    acc[1] = fma(w, v.y[j] - y0, acc[1]);
-    acc[2] += w;
-    if (tc) {
-      acc[3] = fma(v.kvec[j], v.avec[j], acc[3]);
-      acc[4] = fma(v.kvec[j], v.bvec[j], acc[4]);
+  if (tid == 0) s_wmax = 0ull;
+  __syncthreads();
+  if (tc) {   // only the split copy's scale needs max |w|
+    unsigned long long mx = 0ull;
+    for (int j = tid; j < n; j += blockDim.x) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(w_of(j)));
+      mx = b > mx ? b : mx;
     }
-    acc[5] = fmax(acc[5], fabs(w));
+    const uint32_t hi = (uint32_t)(mx >> 32), mh = __reduce_max_sync(0xffffffffu, hi);
+    const uint32_t ml = __reduce_max_sync(0xffffffffu, hi == mh ? (uint32_t)mx : 0u);
+    if (lane == 0) atomicMax(&s_wmax, ((unsigned long long)mh << 32) | ml);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const double x = __shfl_xor_sync(0xffffffffu, acc[q], o);
-      acc[q] = q == 5 ? fmax(acc[q], x) : acc[q] + x;
-    }
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < 6; ++q) red[q][warp] = acc[q];
+  if (warp < 5) {
+    const bool lq = warp < 3;   // an l-phase sum (3 per block) or a w-phase one (2 per block)
+    const double* src = lq ? v.upart + warp : v.upart + 3 * nl + (warp - 3);
+    const int cnt = lq ? nl : nw, stride = lq ? 3 : 2;
+    double t = 0.0;
+    for (int i = lane; i < cnt; i += 32) t += src[(size_t)i * stride];
+    t = warp_sum(t);
+    if (lane == 0) s_sum[warp] = t;
+  }
   __syncthreads();
   if (tid == 0) {
-    double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int w = 0; w < nw; ++w) {
-#pragma unroll
-      for (int q = 0; q < 5; ++q) t[q] += red[q][w];
-      t[5] = fmax(t[5], red[5][w]);
-    }
-    const double d2 = 1.0 + v.jitter - t[0];
+    const double ll = s_sum[0], ka = s_sum[1], kb = s_sum[2], wy = s_sum[3], w1 = s_sum[4];
+    const double wmax = __longlong_as_double((long long)s_wmax);
+    const double d2 = 1.0 + v.jitter - ll;
     const double dinv = (d2 > 0.0 && isfinite(d2)) ? 1.0 / sqrt(d2) : 0.0;
-    if (dinv == 0.0) v.stats->status = BO_ERR_NUMERIC;
     const double dinv2 = dinv * dinv;
     const double yn = v.y[n] - y0;
     s_sc[0] = dinv;
     s_sc[1] = d2;
-    s_sc[2] = (yn - t[1]) * dinv;
-    s_sc[3] = (1.0 - t[2]) * dinv;
-    s_sc[4] = (yn - t[3]) * dinv2;
-    s_sc[5] = (1.0 - t[4]) * dinv2;
-    s_sc[6] = fmax(t[5], 1.0) * dinv;
+    s_sc[2] = (yn - wy) * dinv;
+    s_sc[3] = (1.0 - w1) * dinv;
+    s_sc[4] = (yn - ka) * dinv2;
+    s_sc[5] = (1.0 - kb) * dinv2;
+    s_sc[6] = fmax(wmax, 1.0) * dinv;
     if (tc) {
       // per-row power-of-two scale s with max |row| * s in [2^13, 2^14)
       int e;
       frexp(s_sc[6], &e);                 // amax in [2^(e-1), 2^e)
       s_scale = ldexpf(1.0f, 14 - e);
-      v.xq[xq_index(v.ds, n, v.ds)] = 1.0f / (s_scale * s_scale);
     }
-    v.uvec[n] = s_sc[2];
-    v.evec[n] = s_sc[3];
+    if (slice == 0) {
+      if (dinv == 0.0) v.stats->status = BO_ERR_NUMERIC;
+      if (tc) v.xq[xq_index(v.ds, n, v.ds)] = 1.0f / (s_scale * s_scale);
+      v.uvec[n] = s_sc[2];
+      v.evec[n] = s_sc[3];
+    }
   }
   __syncthreads();
   const double dinv = s_sc[0];
@@ -272,7 +299,7 @@ __device__ __forceinline__ void obs_finish_body(const DevView& v, int n, double 
   const float sc = tc ? s_scale : 0.0f;
   const int eb = split_elem_bytes(v.precision);
   double* row = v.linv + (size_t)n * v.n_max;
-  for (int j = tid; j <= n; j += blockDim.x) {
+  for (int j = slice + nslices * tid; j <= n; j += nslices * (int)blockDim.x) {
     const double w = j < n ? w_of(j) : 0.0;
     const double val = j < n ? -w * dinv : dinv;
     row[j] = val;
@@ -311,14 +338,14 @@ __device__ __forceinline__ void obs_finish_body(const DevView& v, int n, double 
 }
 
 __global__ void obs_finish_kernel(DevView v, int n, double y_mean, double inv_std) {
-  obs_finish_body(v, n, y_mean, inv_std);
+  obs_finish_body(v, n, y_mean, inv_std, 0, 1);
 }
 
 // ---- the same phases over many spaces: block b serves item blocks[b].item ----
 __global__ void obs_k_batch(const ObsItem* items, const ObsBlock* blocks) {
   const ObsBlock b = blocks[blockIdx.x];
   const ObsItem& it = items[b.item];
-  obs_k_body(it.v, it.n, it.idx, it.y_raw, b.local);
+  obs_k_body(it.v, it.n, it.o, b.local);
 }
 
 __global__ void obs_l_batch(const ObsItem* items, const ObsBlock* blocks) {
@@ -336,7 +363,7 @@ __global__ void obs_w_batch(const ObsItem* items, const ObsBlock* blocks) {
 
 __global__ void obs_finish_batch(const ObsItem* items) {
   const ObsItem& it = items[blockIdx.x];
-  obs_finish_body(it.v, it.n, it.y_mean, it.inv_std);
+  obs_finish_body(it.v, it.n, it.o.y_mean, it.o.inv_std, 0, 1);
 }
 
 __global__ void set_visited_batch(const VisitItem* items, int count) {
@@ -443,8 +470,7 @@ __device__ __forceinline__ void l2_prefetch_share(const void* p, size_t bytes, i
   }
 }
 
-__global__ void __launch_bounds__(kFusedThreads) obs_fused_kernel(DevView v, int n, long long idx, double y_raw,
-                                                                  double y_mean, double inv_std) {
+__global__ void __launch_bounds__(kFusedThreads) obs_fused_kernel(DevView v, int n, const __grid_constant__ ObsNew o) {
   pdl_trigger();           // the prediction pass may be launched now (it waits for this update)
   // the phases' inputs into L2 first (an L2 flush between passes leaves them in HBM): the rows of
   // L^-1 (phases l, w), the observations' value indices / coordinates and tables (phase k), the
@@ -469,10 +495,10 @@ __global__ void __launch_bounds__(kFusedThreads) obs_fused_kernel(DevView v, int
   unsigned int phase = 0;
   do {
     // k over all blocks (entry j on block j mod G): its FP64 Matern chains run side by side
-    if (blockIdx.x == 0) obs_record(v, n, idx, y_raw);
+    if (blockIdx.x == 0) obs_record(v, n, o);
     {
       __shared__ KStage ks;
-      k_stage(v, idx, ks);
+      k_stage(v, o, ks);
       for (int j = blockIdx.x + G * threadIdx.x; j < n; j += G * kFusedThreads) obs_kj(v, ks, j);
     }
     if (n > 0) {
@@ -486,7 +512,7 @@ __global__ void __launch_bounds__(kFusedThreads) obs_fused_kernel(DevView v, int
       }
     }
     if (!coop_sync(st, ++phase)) break;
-    if (blockIdx.x == 0) obs_finish_body(v, n, y_mean, inv_std);
+    obs_finish_body(v, n, o.y_mean, o.inv_std, blockIdx.x, G);   // every block: its slice of the row
   } while (false);
   // the last block to leave resets the barrier state for the next update
   __syncthreads();
@@ -542,16 +568,14 @@ int fused_update_grid(int n) {
   return std::min(want, max_blocks);
 }
 
-int launch_observe_update(bool cooperative, const DevView& v, int n, int64_t idx, double y_raw, double y_mean,
-                          double y_std, cudaStream_t s) {
+int launch_observe_update(bool cooperative, const DevView& v, int n, const ObsNew& o, cudaStream_t s) {
   // n = observations fitted before this one; the new one becomes row n.
   if (cooperative) {
     const int grid = fused_update_grid(n);
     if (grid > 0) {
-      long long idx_ll = (long long)idx;
-      double inv_std = 1.0 / y_std;
       DevView vv = v;
-      void* args[] = {&vv, &n, &idx_ll, &y_raw, &y_mean, &inv_std};
+      ObsNew oo = o;
+      void* args[] = {&vv, &n, &oo};
       if (cudaLaunchCooperativeKernel((const void*)obs_fused_kernel, dim3(grid), dim3(kFusedThreads), args, 0, s) ==
           cudaSuccess)
         return 1;
@@ -559,7 +583,7 @@ int launch_observe_update(bool cooperative, const DevView& v, int n, int64_t idx
     }
   }
   int launches = 0;
-  obs_k_kernel<<<(n + 31) / 32 + (n == 0), 32, 0, s>>>(v, n, (long long)idx, y_raw);
+  obs_k_kernel<<<(n + 31) / 32 + (n == 0), 32, 0, s>>>(v, n, o);
   ++launches;
   if (n > 0) {
     obs_l_kernel<<<(n + 7) / 8, 256, 0, s>>>(v, n);
@@ -567,7 +591,7 @@ int launch_observe_update(bool cooperative, const DevView& v, int n, int64_t idx
     obs_w_kernel<<<gw, 256, 0, s>>>(v, n);
     launches += 2;
   }
-  obs_finish_kernel<<<1, 512, 0, s>>>(v, n, y_mean, 1.0 / y_std);
+  obs_finish_kernel<<<1, 512, 0, s>>>(v, n, o.y_mean, o.inv_std);
   ++launches;
   return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
