@@ -64,16 +64,16 @@ LAT_WARM = 50             # warm-up suggest calls before the latency sample
 # dram bytes per launch of the dominant kernel from an ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (null once the source changes)
 TRAFFIC = {
-    "predict_f64": [{"bytes_per_launch": 1119232 + 0, "src_sha": "72387f17a0fb2e5e", "n": 220, "N": 113247,
+    "predict_f64": [{"bytes_per_launch": 1113600 + 0, "src_sha": "a478bc9c3bdf2b0f", "n": 220, "N": 113247,
                      "capture": "profiles/predict_f64_gemm7p_n220.md"}],
     "predict_tc_fp16x3": [
-        {"bytes_per_launch": 10720768 + 2048, "src_sha": "2b082af929346ace", "n": 512, "N": 1032469,
+        {"bytes_per_launch": 10723072 + 2560, "src_sha": "badae9e6ebc24a6c", "n": 512, "N": 1032469,
          "capture": "profiles/predict_tc_fp16x3_gemm9p_n512.md"},
-        {"bytes_per_launch": 1005824 + 512, "src_sha": "2b082af929346ace", "n": 220, "N": 113247,
+        {"bytes_per_launch": 1005568 + 768, "src_sha": "badae9e6ebc24a6c", "n": 220, "N": 113247,
          "capture": "profiles/predict_tc_fp16x3_gemm7p_n220.md"},
     ],
     "predict_tc_tf32x3": [
-        {"bytes_per_launch": 11241728 + 3840, "src_sha": "2b082af929346ace", "n": 512, "N": 1032469,
+        {"bytes_per_launch": 11244800 + 2048, "src_sha": "badae9e6ebc24a6c", "n": 512, "N": 1032469,
          "capture": "profiles/predict_tc_tf32x3_gemm9p_n512.md"},
     ],
 }
