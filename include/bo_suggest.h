@@ -412,6 +412,16 @@ int bo_acquire_noalloc(const void* mu, const void* var, const uint32_t* visited,
  * launch or copy fails. */
 int bo_selftest_waits(int32_t* mbar_status, int32_t* grid_status);
 
+/* Self-test of the exponential of the FP64 prediction pass (no counterpart in
+ * the paper: the pass evaluates e^-t of the Matern covariance, Sec. III-B, with
+ * its own table-driven reduction instead of a general exp).  For the n host
+ * arguments t[i], writes that function's e^-t[i] to out[i] and CUDA's
+ * exp(-t[i]) to ref[i] (both host arrays of n doubles), computed on the current
+ * device.  Synchronous; allocates and frees 24 n bytes of device memory.
+ * Returns BO_ERR_ARG for null arrays or n outside [1, 2^24], BO_ERR_CUDA if
+ * a launch or copy fails. */
+int bo_selftest_exp(const double* t, double* out, double* ref, int32_t n);
+
 /* ---- arithmetic peaks of the current device (measurement) ----------------- */
 /* Issue-rate probes of the units the prediction passes run on, for their
  * roofline denominators (no counterpart in the paper): register-resident

@@ -139,6 +139,7 @@ SIGNATURES = {
     "bo_replay_fetch": (C.c_int, [C.c_void_p, C.POINTER(PassResult), C.c_int32]),
     "bo_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "bo_selftest_waits": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "bo_selftest_exp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "bo_acquire_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                      C.POINTER(AcqParams), C.c_void_p, C.c_void_p]),
     "bo_last_error": (C.c_char_p, []),
@@ -475,6 +476,16 @@ def selftest_waits():
     a, b = C.c_int32(), C.c_int32()
     _check(lib().bo_selftest_waits(C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def selftest_exp(t):
+    """bo_selftest_exp: (the FP64 pass's e^-t, CUDA's exp(-t)) for the float64
+    array t, computed on the current device (see include/bo_suggest.h)."""
+    import numpy as np
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    out, ref = np.empty_like(t), np.empty_like(t)
+    _check(lib().bo_selftest_exp(t.ctypes.data, out.ctypes.data, ref.ctypes.data, int(t.size)))
+    return out, ref
 
 
 def acquire_noalloc(mu_ptr, var_ptr, visited_ptr, f64, params, result_ptr, stream_ptr):

@@ -297,6 +297,8 @@ struct VisitItem {
 
 // ---- launchers (each returns the number of kernels it launched, or -1) ----
 // Self-tests of the bounded device waits (each returns 1 when launched).
+// exp_neg of the FP64 pass and CUDA's exp(-t) for n arguments (device arrays).
+int launch_selftest_exp(const double* t, double* out, double* ref, int n, cudaStream_t s);
 int launch_selftest_mbar(int32_t* status, int* abort_flag, cudaStream_t s);
 int launch_selftest_grid(DevStats* st, cudaStream_t s);
 int launch_observe_update(bool cooperative, const DevView& v, int n, const ObsNew& o, cudaStream_t s);

@@ -12,6 +12,8 @@
 // Each CTA also writes the sum of the variances of its non-evaluated
 // candidates; the acquisition adds those partial sums in block order
 // (deterministic) for the exploration factor (Sec. III-F).
+#include <algorithm>
+
 #include "bo_internal.h"
 
 namespace bo {
@@ -22,10 +24,43 @@ constexpr int kThreads = 256;
 constexpr int kBN = 64;   // output columns of V per pass
 constexpr int kBK = 32;   // j per staged slice of L^-1
 
-__device__ __forceinline__ double matern64(double r, double nu, double c) {
-  double t = c * r;
-  double e = exp(-t);
-  return nu == 1.5 ? (1.0 + t) * e : (1.0 + t + t * t * (1.0 / 3.0)) * e;
+// e^-t for t >= 0 by a table-driven reduction after P. T. P. Tang, "Table-driven
+// implementation of the exponential function in IEEE floating-point
+// arithmetic", ACM Trans. Math. Softw. 15(2), 1989, in the form this kernel
+// needs.  With N = round(-t 64 / ln 2) = 64 m + j (0 <= j < 64) and
+// r = -t - N ln2/64 (|r| <= ln2/128; ln2/64 = L1 + L2, L1 with 36 significant
+// bits so that N L1 is exact), e^-t = 2^m 2^(j/64) e^r with e^r = 1 + r + r^2/2
+// + ... + r^5/120 (the dropped terms are below 4e-17) and 2^(j/64) from tab.
+// N comes from the rounding of x + 1.5 2^52 (the integer sits in the low word),
+// and 2^m is an add to the exponent field.  About 11 FP64 operations.  The
+// Matern evaluation is the only FP64 work of the pass besides the contraction,
+// and the FP64 pipe bounds the pass.  t > 700 gives 0 (e^-700 ~ 1e-304 lies far
+// below every term of mu and sigma^2); NaN stays NaN.
+__device__ __forceinline__ double exp_neg(double t, const double* tab) {
+  const double x = -t * 0x1.71547652b82fep+6;           // -t 64 / ln 2
+  const double sh = x + 0x1.8p52;
+  const double N = sh - 0x1.8p52;
+  const int ni = __double2loint(sh);
+  const double r = fma(-N, 0x1.cf79abc9e3b3ap-46, fma(-N, 0x1.62e42fefa0000p-7, -t));
+  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  const double p = fma(q, r * r, r);
+  const double tj = tab[ni & 63];
+  const double y = fma(tj, p, tj);                      // 2^(j/64) e^r, in [0.99, 2.02)
+  const double e = __hiloint2double(__double2hiint(y) + (ni >> 6) * (1 << 20), __double2loint(y));
+  return t <= 700.0 ? e : (t > 700.0 ? 0.0 : t);
+}
+
+// tab[j] = 2^(j/64), j < 64 (every block fills its own copy in shared memory).
+__device__ __forceinline__ void fill_exp_tab(double* tab) {
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) tab[j] = exp2((double)j * (1.0 / 64.0));
+}
+
+__device__ __forceinline__ double matern64(double r, double nu, double c, const double* tab) {
+  const double t = c * r;
+  const double e = exp_neg(t, tab);
+  return nu == 1.5 ? fma(t, e, e) : (1.0 + t + t * t * (1.0 / 3.0)) * e;
 }
 
 // acc[r][q] += K*[row r][j0 + jj] * L^-1[column q][j0 + jj] over the rows
@@ -88,8 +123,10 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
   uint8_t* Xc = reinterpret_cast<uint8_t*>(meta + 2 * d + 1);
   uint8_t* Cc = Xc + d * n_pad;
   __shared__ double red[kThreads / 32 + 1];
+  __shared__ double exp_tab[64];
 
   const int tid = threadIdx.x;
+  fill_exp_tab(exp_tab);
   const int64_t row0 = (int64_t)blockIdx.x * BM;
   const double c = sqrt(2.0 * v.nu) / v.lengthscale;
 
@@ -130,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1) predict_f64_kernel(DevView v, int
         r2 = fma(diff, diff, r2);
       }
     }
-    Ks[i * ldk + j] = matern64(sqrt(r2), v.nu, c);
+    Ks[i * ldk + j] = matern64(sqrt(r2), v.nu, c, exp_tab);
   }
   for (int e = tid; e < BM * (n_pad - n); e += kThreads) {
     const int i = e / (n_pad - n), j = n + e % (n_pad - n);
@@ -233,7 +270,24 @@ int launch_bm(const DevView& v, int n, cudaStream_t s) {
              : -1;
 }
 
+// Self-test of exp_neg: out[i] = exp_neg(t[i]), ref[i] = CUDA's exp(-t[i]).
+__global__ void selftest_exp_kernel(const double* t, double* out, double* ref, int n) {
+  __shared__ double tab[64];
+  fill_exp_tab(tab);
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    out[i] = exp_neg(t[i], tab);
+    ref[i] = exp(-t[i]);
+  }
+}
+
 }  // namespace
+
+int launch_selftest_exp(const double* t, double* out, double* ref, int n, cudaStream_t s) {
+  if (n < 1) return -1;
+  selftest_exp_kernel<<<std::min((n + 255) / 256, 1024), 256, 0, s>>>(t, out, ref, n);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
 
 int predict_f64_grid(const DevView& v, int n) { return (int)(v.N_pad / (n <= 256 ? 64 : 32)); }
 

@@ -817,6 +817,22 @@ int bo_selftest_waits(int32_t* mbar_status, int32_t* grid_status) {
   return BO_OK;
 }
 
+int bo_selftest_exp(const double* t, double* out, double* ref, int32_t n) {
+  if (!t || !out || !ref) return fail(BO_ERR_ARG, "null argument");
+  if (n < 1 || n > (1 << 24)) return fail(BO_ERR_ARG, "n must be in [1, 2^24]");
+  const size_t bytes = (size_t)n * sizeof(double);
+  double* buf = nullptr;
+  BO_CUDA(cudaMalloc(&buf, 3 * bytes));
+  cudaError_t e = cudaMemcpy(buf, t, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && launch_selftest_exp(buf, buf + n, buf + 2 * (size_t)n, n, nullptr) < 0)
+    e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(out, buf + n, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ref, buf + 2 * (size_t)n, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "self-test of the FP64 pass's exponential");
+  return BO_OK;
+}
+
 int bo_launch_count(const bo_space* s, int64_t* out) {
   if (!s || !out) return fail(BO_ERR_ARG, "null argument");
   *out = s->launches;
