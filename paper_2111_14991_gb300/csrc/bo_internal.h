@@ -90,6 +90,7 @@ struct DevView {
   DevStats* stats;
   TopEntry* acq_partial;     // [max_acq_blocks][3][3]
   int max_acq_blocks;
+  int num_sms;               // multiprocessors of the space's device
   bo_pass_result* results;   // [max_results]
   int max_results;
 };

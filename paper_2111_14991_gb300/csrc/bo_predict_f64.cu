@@ -289,12 +289,22 @@ int launch_selftest_exp(const double* t, double* out, double* ref, int n, cudaSt
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
-int predict_f64_grid(const DevView& v, int n) { return (int)(v.N_pad / (n <= 256 ? 64 : 32)); }
+// Candidates per block: 64 while that still gives every multiprocessor a
+// block, else 32 (a space of 2,560 candidates runs 80 blocks instead of 40 on
+// the FP64 pipes); always 32 for n > 256, where 64 rows of K* no longer fit in
+// shared memory.
+int f64_rows_per_block(const DevView& v, int n) {
+  if (n > 256) return 32;
+  return v.N_pad / 64 >= (int64_t)v.num_sms ? 64 : 32;
+}
+
+int predict_f64_grid(const DevView& v, int n) { return (int)(v.N_pad / f64_rows_per_block(v, n)); }
 
 int launch_predict_f64(const DevView& v, int n, int64_t /*n_unvisited*/, cudaStream_t s) {
   if (n < 1) return -1;
-  if (v.sqd) return n <= 256 ? launch_bm<64, true>(v, n, s) : launch_bm<32, true>(v, n, s);
-  return n <= 256 ? launch_bm<64, false>(v, n, s) : launch_bm<32, false>(v, n, s);
+  const bool wide = f64_rows_per_block(v, n) == 64;
+  if (v.sqd) return wide ? launch_bm<64, true>(v, n, s) : launch_bm<32, true>(v, n, s);
+  return wide ? launch_bm<64, false>(v, n, s) : launch_bm<32, false>(v, n, s);
 }
 
 }  // namespace bo

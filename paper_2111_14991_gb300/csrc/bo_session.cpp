@@ -505,6 +505,7 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, s->device);
   v.max_partials = (int)(N_pad / 32) + num_sms;
   v.max_acq_blocks = 4 * num_sms;
+  v.num_sms = num_sms;
   v.max_results = 1024;
   const size_t fsz = D.precision == BO_PREC_FP64 ? 8 : 4;
   int rc = BO_OK;

@@ -286,25 +286,29 @@ def test_config3_n512_sampled():
     assert np.all(var[idx] <= 1e-8)                  # observed points: variance ~ jitter
 
 
-def wide_value_space():
-    """Three parameters, one of 120 values: the per-parameter tables of squared
-    value differences (120^2 + 8^2 + 6^2 doubles = 116 KB) exceed the 48 KB the
-    library keeps, so distances are formed from coordinate differences."""
-    grids = [np.arange(120) / 119.0, np.arange(8) / 7.0, np.arange(6) / 5.0]
+def wide_value_space(params=3):
+    """Three (5,446 valid) or four (16,534 valid) parameters, one of 120 values:
+    the per-parameter tables of squared value differences (120^2 + 8^2 + 6^2
+    (+ 4^2) doubles = 116 KB) exceed the 48 KB the library keeps, so distances
+    are formed from coordinate differences."""
+    grids = [np.arange(120) / 119.0, np.arange(8) / 7.0, np.arange(6) / 5.0, np.arange(4) / 3.0][:params]
     mesh = np.meshgrid(*grids, indexing="ij")
-    invalid = ((mesh[0] + mesh[1] + mesh[2]) > 2.4).reshape(-1).astype(np.uint8)
+    invalid = (sum(mesh) > 2.4).reshape(-1).astype(np.uint8)
     return grids, invalid
 
 
+@pytest.mark.parametrize("params", [3, 4])
 @pytest.mark.parametrize("n", [60, 300])
 @pytest.mark.parametrize("precision", ["fp64", "fp16x3"])
-def test_untabulated_distances(n, precision):
+def test_untabulated_distances(n, precision, params):
     """Spaces whose value tables exceed 48 KB take the difference-based distances
-    (the TAB = false FP64 prediction instantiations, BM = 64 and 32, and the
-    update's covariance row): mu and sigma against the oracle, zero variance at
-    the observed points (update and prediction agree on K)."""
+    (the TAB = false FP64 prediction instantiations and the update's covariance
+    row): 64 candidates per block for 16,534 candidates at n = 60, 32 for
+    n = 300 and for 5,446 candidates, which would not give every multiprocessor
+    a block of 64.  mu and sigma against the oracle, zero variance at the
+    observed points (update and prediction agree on K)."""
     from paper_2111_14991_gb300 import Space
-    grids, invalid = wide_value_space()
+    grids, invalid = wide_value_space(params)
     flat, codes = O.valid_list([len(g) for g in grids], invalid)
     coords = O.candidate_coords(grids, codes)
     rng = np.random.default_rng(n)
@@ -322,7 +326,7 @@ def test_untabulated_distances(n, precision):
     # sigma ~ 3e-3 next to them, where the FP32 rounding of sigma^2 (~1e-5)
     # alone moves sigma by its square root: an envelope there
     tol = FP64 if precision == "fp64" else dict(rel=1e-3 if n <= 60 else 5e-3, floor=1.0)
-    parity_report(f"wide-value n={n} {precision}", mu, rmu, var, rvar, tol["rel"])
+    parity_report(f"wide-value d={params} n={n} {precision}", mu, rmu, var, rvar, tol["rel"])
     assert_close(mu, rmu, what="mu", **tol)
     assert_close(np.sqrt(var), np.sqrt(rvar), what="sigma", **tol)
     if precision == "fp64":
