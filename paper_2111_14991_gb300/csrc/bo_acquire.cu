@@ -8,6 +8,7 @@
 // keeps the k best (score, index) per function: per thread, then merged
 // across the warp with shuffles, across the block in shared memory, and
 // across blocks by the last block to finish.  Ties go to the lower index.
+#include <algorithm>
 #include <cfloat>
 #include <cstdlib>
 #include <climits>
@@ -209,7 +210,8 @@ __device__ __forceinline__ void acquire_body(const AcqDev& v, const PassArgs& a,
 #pragma unroll
   for (int q = 0; q < 3; ++q) top_init(top[q]);
   const int64_t stride = (int64_t)nblocks * kThreads;
-  for (int64_t i = (int64_t)block * kThreads + threadIdx.x; i < v.N; i += stride) {
+  const int64_t first = v.spread ? block + (int64_t)nblocks * threadIdx.x : (int64_t)block * kThreads + threadIdx.x;
+  for (int64_t i = first; i < v.N; i += stride) {
     if ((v.visited[i >> 5] >> (i & 31)) & 1u) continue;
     const T m = mu[i];
     const T vv = var[i];
@@ -344,9 +346,17 @@ int acquire_grid(int64_t n_cand, int max_blocks, int per_thread) {
 }
 
 int launch_acquire(const AcqDev& v, const PassArgs& a, bool f64, cudaStream_t s) {
-  const int grid = acquire_grid(v.N, v.max_blocks, 2);
-  const cudaError_t e = f64 ? launch_ex(acquire_kernel<double>, dim3(grid), dim3(kThreads), 0, s, pdl_enabled(), v, a)
-                            : launch_ex(acquire_kernel<float>, dim3(grid), dim3(kThreads), 0, s, pdl_enabled(), v, a);
+  int grid = acquire_grid(v.N, v.max_blocks, 2);
+  AcqDev w = v;
+  if (f64 && v.min_blocks > grid) {
+    // few candidates for the narrow FP64 pipes: one block per multiprocessor
+    // (at least 16 candidates each), candidates dealt round-robin over them
+    const int64_t want = std::max<int64_t>((v.N + 15) / 16, grid);
+    grid = (int)std::min<int64_t>(std::min<int64_t>(v.max_blocks, v.min_blocks), want);
+    w.spread = 1;
+  }
+  const cudaError_t e = f64 ? launch_ex(acquire_kernel<double>, dim3(grid), dim3(kThreads), 0, s, pdl_enabled(), w, a)
+                            : launch_ex(acquire_kernel<float>, dim3(grid), dim3(kThreads), 0, s, pdl_enabled(), w, a);
   return e == cudaSuccess ? 1 : -1;
 }
 
@@ -373,6 +383,7 @@ int launch_acquire(const DevView& v, const PassArgs& a, cudaStream_t s) {
   ad.partial = v.acq_partial;
   ad.counter = &v.stats->k2_done;
   ad.max_blocks = v.max_acq_blocks;
+  ad.min_blocks = v.num_sms;
   ad.result = v.results + a.result_slot;
   return launch_acquire(ad, a, v.precision == BO_PREC_FP64, s);
 }

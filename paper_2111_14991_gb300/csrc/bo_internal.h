@@ -215,6 +215,11 @@ struct AcqDev {
   unsigned int* counter;     // last-block counter, 0 between launches
   int max_blocks;
   bo_pass_result* result;
+  // FP64 posteriors of a small space: at least min_blocks blocks (one per
+  // multiprocessor), candidates dealt round-robin over the blocks (spread), so
+  // that the FP64 scoring runs on every FP64 pipe; 0 keeps the plain grid
+  int min_blocks = 0;
+  int spread = 0;
 };
 
 // One space as the tensor-core pass sees it (device pointers and sizes).
