@@ -64,7 +64,7 @@ LAT_WARM = 50             # warm-up suggest calls before the latency sample
 # dram bytes per launch of the dominant kernel from an ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (null once the source changes)
 TRAFFIC = {
-    "predict_f64": [{"bytes_per_launch": 1113600 + 0, "src_sha": "a478bc9c3bdf2b0f", "n": 220, "N": 113247,
+    "predict_f64": [{"bytes_per_launch": 1228544 + 0, "src_sha": "536356e59795c5b1", "n": 220, "N": 113247,
                      "capture": "profiles/predict_f64_gemm7p_n220.md"}],
     "predict_tc_fp16x3": [
         {"bytes_per_launch": 10723072 + 2560, "src_sha": "badae9e6ebc24a6c", "n": 512, "N": 1032469,
