@@ -478,10 +478,12 @@ __device__ __forceinline__ void split2(uint64_t kv, uint32_t& hi, uint32_t& lo) 
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(rb), "f"(ra));
 }
 
+// x rounded to TF32 (10 explicit mantissa bits), to nearest with ties away from
+// zero: half an ulp of the 10-bit mantissa added to the magnitude bits, the 13
+// low bits cleared (a carry moves into the exponent as in any rounding).  Two
+// integer operations; the same bits as cvt.rna.tf32.f32 for every finite x.
 __device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t u;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
-  return u;
+  return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
