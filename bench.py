@@ -67,13 +67,13 @@ TRAFFIC = {
     "predict_f64": [{"bytes_per_launch": 1228544 + 0, "src_sha": "536356e59795c5b1", "n": 220, "N": 113247,
                      "capture": "profiles/predict_f64_gemm7p_n220.md"}],
     "predict_tc_fp16x3": [
-        {"bytes_per_launch": 10723072 + 2560, "src_sha": "badae9e6ebc24a6c", "n": 512, "N": 1032469,
+        {"bytes_per_launch": 10722048 + 3072, "src_sha": "6a86536e3304ae4b", "n": 512, "N": 1032469,
          "capture": "profiles/predict_tc_fp16x3_gemm9p_n512.md"},
-        {"bytes_per_launch": 1005568 + 768, "src_sha": "badae9e6ebc24a6c", "n": 220, "N": 113247,
+        {"bytes_per_launch": 1004032 + 0, "src_sha": "6a86536e3304ae4b", "n": 220, "N": 113247,
          "capture": "profiles/predict_tc_fp16x3_gemm7p_n220.md"},
     ],
     "predict_tc_tf32x3": [
-        {"bytes_per_launch": 11244800 + 2048, "src_sha": "badae9e6ebc24a6c", "n": 512, "N": 1032469,
+        {"bytes_per_launch": 11245568 + 1792, "src_sha": "6a86536e3304ae4b", "n": 512, "N": 1032469,
          "capture": "profiles/predict_tc_tf32x3_gemm9p_n512.md"},
     ],
 }
