@@ -333,7 +333,10 @@ typedef struct bo_server_stats {
 
 int bo_server_create(const bo_server_config* config, bo_server** out);
 /* Register a session (the descriptor's arrays are copied); *session_out
- * receives its id.  BO_ERR_NOMEM if it could never fit the budget.  The
+ * receives its id.  The descriptor is checked at once as bo_space_create
+ * checks it (BO_ERR_ARG, nothing registered); BO_ERR_NOMEM if the session
+ * could never fit the budget.  A session that later fails to be created on
+ * the device completes its queued requests with that call's code.  The
  * descriptor's alloc / free / stream fields are ignored (the server's apply). */
 int bo_server_open(bo_server* server, const bo_space_desc* desc, int64_t* session_out);
 /* Queue a request: observe (idx, value) first if observe_idx >= 0, then

@@ -85,13 +85,15 @@ void admit(bo_server* S) {
     d.alloc_ctx = S->cfg.alloc_ctx;
     d.stream = S->cfg.stream;
     bo_space* sp = nullptr;
-    if (bo_space_create(&d, &sp) != BO_OK) {   // could not allocate after all: reject it
+    // the descriptor passed its checks at open: what can fail here is the
+    // device (memory, a launch); the requests carry that code
+    if (const int rc = bo_space_create(&d, &sp); rc != BO_OK) {
       ++S->stats.rejected;
       for (auto& r : ss.pending) {
         bo_completion c{};
         c.tag = r.tag;
         c.session = ss.id;
-        c.status = BO_ERR_NOMEM;
+        c.status = rc;
         c.idx = -1;
         c.t_submit = r.t_submit;
         c.t_done = now_s(S);
@@ -250,17 +252,16 @@ int bo_server_create(const bo_server_config* cfg, bo_server** out) {
 }
 
 int bo_server_open(bo_server* S, const bo_space_desc* desc, int64_t* session_out) {
-  if (!S || !desc || !session_out || !desc->n_values || !desc->values || desc->d < 1 || desc->d > BO_MAX_PARAMS)
-    return fail(BO_ERR_ARG, "bad argument");
+  if (!S || !desc || !session_out) return fail(BO_ERR_ARG, "null argument");
+  // the whole descriptor is checked here, as bo_space_create checks it, so that a
+  // bad one is refused at once instead of failing its requests at admission
+  int64_t total = 0;
+  if (const int rc = check_space_desc(*desc, &total); rc != BO_OK) return rc;
   Session ss;
   ss.desc = *desc;
-  int64_t total = 1;
   for (int p = 0; p < desc->d; ++p) {
-    if (desc->n_values[p] < 1 || desc->n_values[p] > BO_MAX_VALUES) return fail(BO_ERR_ARG, "bad value list");
     ss.n_values.push_back(desc->n_values[p]);
     ss.values.emplace_back(desc->values[p], desc->values[p] + desc->n_values[p]);
-    total *= desc->n_values[p];
-    if (total > ((int64_t)1 << 40)) return fail(BO_ERR_ARG, "search space too large");
   }
   for (auto& v : ss.values) ss.value_ptrs.push_back(v.data());
   int64_t n_valid = total;
@@ -269,6 +270,9 @@ int bo_server_open(bo_server* S, const bo_space_desc* desc, int64_t* session_out
     n_valid = 0;
     for (uint8_t m : ss.mask) n_valid += !m;
   }
+  if (n_valid == 0) return fail(BO_ERR_ARG, "no valid configuration");
+  if (desc->precision != BO_PREC_FP64 && n_valid >= (int64_t)0xFFFFFFFF)
+    return fail(BO_ERR_ARG, "reduced precision holds fewer than 2^32 - 1 valid configurations");
   ss.est_bytes = space_device_bytes(desc->d, n_valid, desc->n_max, desc->precision, S->num_sms);
   std::lock_guard<std::mutex> lk(S->mu);
   if (ss.est_bytes > S->cfg.budget_bytes) {

@@ -389,6 +389,34 @@ int suggest_finish(bo_space* s, const bo_pass_result& r, int64_t* idx_out, bo_su
   return BO_OK;
 }
 
+// Every check of a space descriptor that needs no device: the fields, the
+// value lists and the size of the product (*total_out); the mask's content is
+// the caller's to check.  BO_OK, or BO_ERR_ARG with the message set.
+int check_space_desc(const bo_space_desc& D, int64_t* total_out) {
+  if (D.d < 1 || D.d > BO_MAX_PARAMS) return fail(BO_ERR_ARG, "d = %d not in [1, %d]", D.d, BO_MAX_PARAMS);
+  if (!D.n_values || !D.values) return fail(BO_ERR_ARG, "n_values / values missing");
+  if (!(D.nu == 1.5 || D.nu == 2.5)) return fail(BO_ERR_ARG, "nu must be 1.5 or 2.5");
+  if (!(D.lengthscale > 0) || !(D.jitter >= 0)) return fail(BO_ERR_ARG, "bad lengthscale / jitter");
+  if (D.af < BO_AF_EI || D.af > BO_AF_ADV_MULTI) return fail(BO_ERR_ARG, "bad af");
+  if (D.explore != BO_EXPLORE_CV && D.explore != BO_EXPLORE_CONST) return fail(BO_ERR_ARG, "bad explore");
+  if (D.precision < BO_PREC_FP64 || D.precision > BO_PREC_TF32X3) return fail(BO_ERR_ARG, "bad precision");
+  if (D.n_max < 1 || D.n_max > BO_MAX_OBS) return fail(BO_ERR_ARG, "n_max not in [1, %d]", BO_MAX_OBS);
+  if (D.skip_threshold < 0 || D.n_init < 0 || D.init_designs < 0) return fail(BO_ERR_ARG, "negative count");
+  if (D.init_mode < BO_INIT_RANDOM || D.init_mode > BO_INIT_MAXIMIN) return fail(BO_ERR_ARG, "bad init_mode");
+  int64_t total = 1;
+  for (int p = 0; p < D.d; ++p) {
+    if (D.n_values[p] < 1 || D.n_values[p] > BO_MAX_VALUES || !D.values[p])
+      return fail(BO_ERR_ARG, "parameter %d: bad value list", p);
+    for (int i = 0; i < D.n_values[p]; ++i)
+      if (!(D.values[p][i] >= 0.0 && D.values[p][i] <= 1.0))
+        return fail(BO_ERR_ARG, "parameter %d value %d not normalized to [0, 1]", p, i);
+    total *= D.n_values[p];
+    if (total > ((int64_t)1 << 40)) return fail(BO_ERR_ARG, "search space too large");
+  }
+  *total_out = total;
+  return BO_OK;
+}
+
 }  // namespace host
 }  // namespace bo
 
@@ -420,26 +448,8 @@ int bo_space_create(const bo_space_desc* desc, bo_space** out) {
   if (!desc || !out) return fail(BO_ERR_ARG, "null argument");
   *out = nullptr;
   const bo_space_desc& D = *desc;
-  if (D.d < 1 || D.d > BO_MAX_PARAMS) return fail(BO_ERR_ARG, "d = %d not in [1, %d]", D.d, BO_MAX_PARAMS);
-  if (!D.n_values || !D.values) return fail(BO_ERR_ARG, "n_values / values missing");
-  if (!(D.nu == 1.5 || D.nu == 2.5)) return fail(BO_ERR_ARG, "nu must be 1.5 or 2.5");
-  if (!(D.lengthscale > 0) || !(D.jitter >= 0)) return fail(BO_ERR_ARG, "bad lengthscale / jitter");
-  if (D.af < BO_AF_EI || D.af > BO_AF_ADV_MULTI) return fail(BO_ERR_ARG, "bad af");
-  if (D.explore != BO_EXPLORE_CV && D.explore != BO_EXPLORE_CONST) return fail(BO_ERR_ARG, "bad explore");
-  if (D.precision < BO_PREC_FP64 || D.precision > BO_PREC_TF32X3) return fail(BO_ERR_ARG, "bad precision");
-  if (D.n_max < 1 || D.n_max > BO_MAX_OBS) return fail(BO_ERR_ARG, "n_max not in [1, %d]", BO_MAX_OBS);
-  if (D.skip_threshold < 0 || D.n_init < 0 || D.init_designs < 0) return fail(BO_ERR_ARG, "negative count");
-  if (D.init_mode < BO_INIT_RANDOM || D.init_mode > BO_INIT_MAXIMIN) return fail(BO_ERR_ARG, "bad init_mode");
-  int64_t total = 1;
-  for (int p = 0; p < D.d; ++p) {
-    if (D.n_values[p] < 1 || D.n_values[p] > BO_MAX_VALUES || !D.values[p])
-      return fail(BO_ERR_ARG, "parameter %d: bad value list", p);
-    for (int i = 0; i < D.n_values[p]; ++i)
-      if (!(D.values[p][i] >= 0.0 && D.values[p][i] <= 1.0))
-        return fail(BO_ERR_ARG, "parameter %d value %d not normalized to [0, 1]", p, i);
-    total *= D.n_values[p];
-    if (total > ((int64_t)1 << 40)) return fail(BO_ERR_ARG, "search space too large");
-  }
+  int64_t total = 0;
+  if (const int rc = check_space_desc(D, &total); rc != BO_OK) return rc;
 
   bo_space* s = new (std::nothrow) bo_space();
   if (!s) return fail(BO_ERR_NOMEM, "host allocation failed");

@@ -206,6 +206,9 @@ int initial_design(const std::vector<std::vector<double>>& values, int64_t n_val
 int dalloc(bo_space* s, size_t bytes, void** out);
 // Device bytes bo_space_create allocates for these sizes, and those a space holds.
 size_t space_device_bytes(int d, int64_t N, int n_max, int precision, int num_sms);
+// The device-free checks of a space descriptor (fields, value lists, size of
+// the product, returned in *total_out): BO_OK or BO_ERR_ARG with the message set.
+int check_space_desc(const bo_space_desc& D, int64_t* total_out);
 size_t space_bytes(const bo_space* s);
 void y_stats(const bo_space* s, double* mean, double* std_, double* ymin);
 // Scalars of a prediction pass with the given active AFs (takes the

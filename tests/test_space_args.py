@@ -97,3 +97,37 @@ def test_null_arguments(lib):
     desc.values = None
     assert lib.bo_space_create(C.byref(desc), C.byref(out)) == BO_ERR_ARG
     assert "missing" in lib.bo_last_error().decode()
+
+
+def test_server_open_checks_the_descriptor(lib):
+    """bo_server_open refuses a bad descriptor at once, with the same checks and
+    messages as bo_space_create, and registers nothing; a good one is queued.
+    (The server's worker only waits here: nothing is admitted without a device
+    budget, so this runs without a GPU.)"""
+    from paper_2111_14991_gb300 import bo
+    cfg = bo.ServerConfig()
+    cfg.budget_bytes = 1          # below any session: a good descriptor gets BO_ERR_NOMEM, not BO_ERR_ARG
+    cfg.max_sessions = 4
+    srv = C.c_void_p()
+    assert lib.bo_server_create(C.byref(cfg), C.byref(srv)) == 0
+    try:
+        sid = C.c_int64(-1)
+        for field, value, words in (("nu", 0.5, "nu"), ("precision", 9, "precision"), ("n_max", 0, "n_max"),
+                                    ("lengthscale", -1.0, "lengthscale")):
+            desc, keep = bo.make_desc(GRIDS)
+            setattr(desc, field, value)
+            assert lib.bo_server_open(srv, C.byref(desc), C.byref(sid)) == BO_ERR_ARG
+            assert words in lib.bo_last_error().decode()
+        desc, keep = bo.make_desc([np.linspace(0.0, 1.0, 3), np.array([0.0, 2.0])])
+        assert lib.bo_server_open(srv, C.byref(desc), C.byref(sid)) == BO_ERR_ARG
+        assert "not normalized" in lib.bo_last_error().decode()
+        desc, keep = bo.make_desc(GRIDS, np.ones(12, dtype=np.uint8))
+        assert lib.bo_server_open(srv, C.byref(desc), C.byref(sid)) == BO_ERR_ARG
+        assert "no valid configuration" in lib.bo_last_error().decode()
+        desc, keep = bo.make_desc(GRIDS)
+        assert lib.bo_server_open(srv, C.byref(desc), C.byref(sid)) == 6     # BO_ERR_NOMEM: over the budget
+        st = bo.ServerStats()
+        assert lib.bo_server_stats_get(srv, C.byref(st)) == 0
+        assert st.queued == 0 and st.admitted == 0
+    finally:
+        assert lib.bo_server_destroy(srv) == 0
